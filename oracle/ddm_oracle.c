@@ -1,0 +1,416 @@
+/*
+ * CPU oracle for Data Distribution Management matching
+ * (Marzolla, D'Angelo, Mandrioli, "A Parallel Data Distribution Management
+ * Algorithm", DS-RT 2013).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, obviously correct
+ * statement of what the GPU library computes.  Only the test suite, the
+ * smoke check and the benchmark's CPU-baseline leg load it; the library's
+ * product path never does.  It shares no code, header or constant with the
+ * CUDA path.
+ *
+ * Problem (Section III): subscription extents S_1..S_n and update extents
+ * U_1..U_m, each a d-rectangle; report every pair (S_i, U_j) whose
+ * intersection is non-empty.  Ids are 0-based input indices here (the paper
+ * numbers from 1).
+ *
+ * Coordinates arrive as float32 in structure-of-arrays layout: row k
+ * (dimension k) of a set with c extents starts at offset k*c.  All
+ * arithmetic below is comparisons, carried out on values widened to double
+ * (exact for float32 inputs, so no rounding enters).
+ *
+ * Readings of the paper taken here:
+ *  - Closed vs open segments.  Alg. 1 writes strict comparisons, while the
+ *    segments are written as closed intervals [low, high].  The default rule
+ *    is closed (x.low <= y.high and y.low <= x.high); flag OPEN selects the
+ *    literal strict test of Alg. 1.
+ *  - Under the closed rule the right-subtree descent of Alg. 4 becomes
+ *    q.upper >= x.in.lower (equal lower keys may sit in the right subtree).
+ *  - Tree order (Section IV): by lower bound, ties by upper bound; remaining
+ *    ties by id (the paper is silent; this only fixes an order).
+ *
+ * Parity: pinned.  BF and ITM are checked against each other, against
+ * closed-form lattice counts, against the worked example of Fig. 1 and
+ * against BITS counting (Section II) by the CPU test suite.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OPEN 1u
+
+/* ------------------------------------------------------------------ */
+/* Alg. 1, Intersect-1D                                                */
+/* ------------------------------------------------------------------ */
+static int intersect_1d(double xlo, double xhi, double ylo, double yhi, int open)
+{
+    if (open)
+        return xlo < yhi && ylo < xhi;          /* Alg. 1 as printed */
+    return xlo <= yhi && ylo <= xhi;            /* closed segments */
+}
+
+/* Section III-A: two d-rectangles intersect iff all their projections do. */
+static int intersect_d(int d,
+                       const float *alo, const float *ahi, uint64_t astride, uint64_t ai,
+                       const float *blo, const float *bhi, uint64_t bstride, uint64_t bi,
+                       int open)
+{
+    for (int k = 0; k < d; ++k) {
+        if (!intersect_1d(alo[k * astride + ai], ahi[k * astride + ai],
+                          blo[k * bstride + bi], bhi[k * bstride + bi], open))
+            return 0;
+    }
+    return 1;
+}
+
+int oracle_intersect_1d(double xlo, double xhi, double ylo, double yhi, uint32_t flags)
+{
+    return intersect_1d(xlo, xhi, ylo, yhi, (flags & ORACLE_OPEN) != 0);
+}
+
+/* SplitMix64 output function (Steele, Lea, Flood, OOPSLA 2014), used only
+ * to give each update an order-independent digest of its matched ids. */
+uint64_t oracle_mix64(uint64_t z)
+{
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* ------------------------------------------------------------------ */
+/* Alg. 2, Brute Force, extended to d dimensions (Section III-A).      */
+/* The pair test of every (S_i, U_j) is independent; the loop runs     */
+/* over updates outside so that each update's pairs come out together, */
+/* in ascending subscription id.                                       */
+/* ------------------------------------------------------------------ */
+uint64_t oracle_bf(int d,
+                   const float *upd_lo, const float *upd_hi, uint32_t m,
+                   const float *sub_lo, const float *sub_hi, uint32_t n,
+                   uint32_t flags,
+                   uint32_t *counts,                  /* [m] or NULL */
+                   uint64_t *digests,                 /* [m] or NULL */
+                   uint32_t *out_upd, uint32_t *out_sub, uint64_t cap)
+{
+    const int open = (flags & ORACLE_OPEN) != 0;
+    uint64_t K = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+        uint32_t c = 0;
+        uint64_t dig = 0;
+        for (uint32_t i = 0; i < n; ++i) {
+            if (intersect_d(d, sub_lo, sub_hi, n, i, upd_lo, upd_hi, m, j, open)) {
+                if (out_upd && K < cap) {
+                    out_upd[K] = j;
+                    out_sub[K] = i;
+                }
+                ++K;
+                ++c;
+                dig += oracle_mix64(i);
+            }
+        }
+        if (counts) counts[j] = c;
+        if (digests) digests[j] = dig;
+    }
+    return K;
+}
+
+/* ------------------------------------------------------------------ */
+/* Interval tree (Section IV): augmented AVL tree.                     */
+/* Each node holds one interval x.in (dimension 0 of a subscription),  */
+/* plus maxupper / minlower of the subtree rooted at it.               */
+/* ------------------------------------------------------------------ */
+typedef struct {
+    double lo, hi;          /* x.in */
+    uint32_t id;            /* x.in.id */
+    double maxupper, minlower;
+    int32_t left, right;    /* -1 = null */
+    int32_t height;
+} it_node;
+
+typedef struct {
+    it_node *v;
+    int32_t root;
+    uint32_t size;
+} it_tree;
+
+static int32_t h_of(const it_tree *t, int32_t x) { return x < 0 ? 0 : t->v[x].height; }
+
+/* Recompute the augmented fields of x from its interval and children. */
+static void it_fix(it_tree *t, int32_t x)
+{
+    it_node *p = &t->v[x];
+    double mu = p->hi, ml = p->lo;
+    int32_t hl = h_of(t, p->left), hr = h_of(t, p->right);
+    if (p->left >= 0) {
+        if (t->v[p->left].maxupper > mu) mu = t->v[p->left].maxupper;
+        if (t->v[p->left].minlower < ml) ml = t->v[p->left].minlower;
+    }
+    if (p->right >= 0) {
+        if (t->v[p->right].maxupper > mu) mu = t->v[p->right].maxupper;
+        if (t->v[p->right].minlower < ml) ml = t->v[p->right].minlower;
+    }
+    p->maxupper = mu;
+    p->minlower = ml;
+    p->height = 1 + (hl > hr ? hl : hr);
+}
+
+static int32_t rot_right(it_tree *t, int32_t y)
+{
+    int32_t x = t->v[y].left;
+    t->v[y].left = t->v[x].right;
+    t->v[x].right = y;
+    it_fix(t, y);
+    it_fix(t, x);
+    return x;
+}
+
+static int32_t rot_left(it_tree *t, int32_t x)
+{
+    int32_t y = t->v[x].right;
+    t->v[x].right = t->v[y].left;
+    t->v[y].left = x;
+    it_fix(t, x);
+    it_fix(t, y);
+    return y;
+}
+
+/* Key order: lower bound, then upper bound, then id. */
+static int key_less(const it_node *a, const it_node *b)
+{
+    if (a->lo < b->lo) return 1;
+    if (b->lo < a->lo) return 0;
+    if (a->hi < b->hi) return 1;
+    if (b->hi < a->hi) return 0;
+    return a->id < b->id;
+}
+
+/* Usual AVL insertion; augmented fields are refreshed on the way back to the
+ * root and through every rotation, so they stay exact (Section IV). */
+static int32_t it_insert(it_tree *t, int32_t x, int32_t z)
+{
+    if (x < 0) return z;
+    if (key_less(&t->v[z], &t->v[x]))
+        t->v[x].left = it_insert(t, t->v[x].left, z);
+    else
+        t->v[x].right = it_insert(t, t->v[x].right, z);
+    it_fix(t, x);
+    int32_t bal = h_of(t, t->v[x].left) - h_of(t, t->v[x].right);
+    if (bal > 1) {
+        if (h_of(t, t->v[t->v[x].left].left) < h_of(t, t->v[t->v[x].left].right))
+            t->v[x].left = rot_left(t, t->v[x].left);
+        return rot_right(t, x);
+    }
+    if (bal < -1) {
+        if (h_of(t, t->v[t->v[x].right].right) < h_of(t, t->v[t->v[x].right].left))
+            t->v[x].right = rot_right(t, t->v[x].right);
+        return rot_left(t, x);
+    }
+    return x;
+}
+
+/* Interval-Tree-Create (Alg. 5): n insertions of dimension-0 segments. */
+static int it_create(it_tree *t, const float *lo0, const float *hi0, uint32_t n)
+{
+    t->v = (it_node *)malloc((size_t)(n ? n : 1) * sizeof(it_node));
+    if (!t->v) return -1;
+    t->root = -1;
+    t->size = n;
+    for (uint32_t i = 0; i < n; ++i) {
+        it_node *p = &t->v[i];
+        p->lo = lo0[i];
+        p->hi = hi0[i];
+        p->id = i;
+        p->left = p->right = -1;
+        p->height = 1;
+        p->maxupper = p->hi;
+        p->minlower = p->lo;
+        t->root = it_insert(t, t->root, (int32_t)i);
+    }
+    return 0;
+}
+
+typedef struct {
+    int d, open;
+    const float *ulo, *uhi; uint32_t m; uint32_t j;   /* the query U_j */
+    const float *slo, *shi; uint32_t n;
+    uint32_t count;
+    uint64_t digest;
+    uint32_t *out_sub; uint64_t cap; uint64_t K;      /* optional pair list */
+} it_query;
+
+/* Interval-Query (Alg. 4).  Pruning uses maxupper / minlower of the
+ * subtree; the node's own interval is tested with Intersect-1D; remaining
+ * dimensions 1..d-1 of a dimension-0 hit are tested before reporting. */
+static void it_query_rec(const it_tree *t, int32_t x, it_query *q)
+{
+    if (x < 0) return;
+    const it_node *p = &t->v[x];
+    const double ql = q->ulo[q->j], qh = q->uhi[q->j];
+    if (p->maxupper < ql || p->minlower > qh) return;
+    it_query_rec(t, p->left, q);
+    if (intersect_1d(p->lo, p->hi, ql, qh, q->open)) {
+        int ok = 1;
+        for (int k = 1; k < q->d && ok; ++k)
+            ok = intersect_1d(q->slo[(uint64_t)k * q->n + p->id], q->shi[(uint64_t)k * q->n + p->id],
+                              q->ulo[(uint64_t)k * q->m + q->j], q->uhi[(uint64_t)k * q->m + q->j],
+                              q->open);
+        if (ok) {
+            if (q->out_sub && q->K < q->cap) q->out_sub[q->K] = p->id;
+            ++q->K;
+            ++q->count;
+            q->digest += oracle_mix64(p->id);
+        }
+    }
+    /* Right subtree keys have lower >= p->lo. */
+    if (q->open ? (qh > p->lo) : (qh >= p->lo))
+        it_query_rec(t, p->right, q);
+}
+
+/* IntTree-Matching (Alg. 5) with per-update counts and digests; the loop
+ * over updates is split across threads as in the paper's parallel ITM
+ * (Section IV, "Parallelizing ITM"): every query only reads the tree. */
+uint64_t oracle_itm_count(int d,
+                          const float *upd_lo, const float *upd_hi, uint32_t m,
+                          const float *sub_lo, const float *sub_hi, uint32_t n,
+                          uint32_t flags, int nthreads,
+                          uint32_t *counts, uint64_t *digests)
+{
+    it_tree t;
+    if (it_create(&t, sub_lo, sub_hi, n) != 0) return UINT64_MAX;
+    uint64_t K = 0;
+#ifdef _OPENMP
+    if (nthreads < 1) nthreads = 1;
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : K) num_threads(nthreads)
+#endif
+    for (int64_t jj = 0; jj < (int64_t)m; ++jj) {
+        it_query q;
+        memset(&q, 0, sizeof q);
+        q.d = d; q.open = (flags & ORACLE_OPEN) != 0;
+        q.ulo = upd_lo; q.uhi = upd_hi; q.m = m; q.j = (uint32_t)jj;
+        q.slo = sub_lo; q.shi = sub_hi; q.n = n;
+        it_query_rec(&t, t.root, &q);
+        if (counts) counts[jj] = q.count;
+        if (digests) digests[jj] = q.digest;
+        K += q.count;
+    }
+    free(t.v);
+    return K;
+}
+
+/* Sequential ITM producing the pair list, update by update; within an
+ * update the pairs come in tree (in-order) order. */
+uint64_t oracle_itm_pairs(int d,
+                          const float *upd_lo, const float *upd_hi, uint32_t m,
+                          const float *sub_lo, const float *sub_hi, uint32_t n,
+                          uint32_t flags,
+                          uint32_t *out_upd, uint32_t *out_sub, uint64_t cap)
+{
+    it_tree t;
+    if (it_create(&t, sub_lo, sub_hi, n) != 0) return UINT64_MAX;
+    uint64_t K = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+        it_query q;
+        memset(&q, 0, sizeof q);
+        q.d = d; q.open = (flags & ORACLE_OPEN) != 0;
+        q.ulo = upd_lo; q.uhi = upd_hi; q.m = m; q.j = j;
+        q.slo = sub_lo; q.shi = sub_hi; q.n = n;
+        q.out_sub = out_sub ? out_sub + (K < cap ? K : cap) : NULL;
+        q.cap = K < cap ? cap - K : 0;
+        it_query_rec(&t, t.root, &q);
+        if (out_upd)
+            for (uint64_t r = K; r < K + q.count && r < cap; ++r) out_upd[r] = j;
+        K += q.count;
+    }
+    free(t.v);
+    return K;
+}
+
+/* In-order sequence of the interval tree: subscription ids sorted by
+ * (lower, upper, id) on dimension 0; also reports the tree height. */
+static void inorder(const it_tree *t, int32_t x, uint32_t *out, uint32_t *pos)
+{
+    if (x < 0) return;
+    inorder(t, t->v[x].left, out, pos);
+    out[(*pos)++] = t->v[x].id;
+    inorder(t, t->v[x].right, out, pos);
+}
+
+int oracle_tree_order(const float *lo0, const float *hi0, uint32_t n, uint32_t *order, int32_t *height)
+{
+    it_tree t;
+    if (it_create(&t, lo0, hi0, n) != 0) return -1;
+    uint32_t pos = 0;
+    inorder(&t, t.root, order, &pos);
+    if (height) *height = h_of(&t, t.root);
+    free(t.v);
+    return 0;
+}
+
+/* ------------------------------------------------------------------ */
+/* BITS counting (Layer et al., Section II), d = 1, closed rule only:  */
+/* |B| minus the intervals ending before q.low minus those starting    */
+/* after q.high; for lo <= hi the two events are disjoint.             */
+/* ------------------------------------------------------------------ */
+static int cmp_float(const void *a, const void *b)
+{
+    float x = *(const float *)a, y = *(const float *)b;
+    return (x > y) - (x < y);
+}
+
+/* number of v[] strictly less than key (v sorted ascending) */
+static uint32_t count_less(const float *v, uint32_t n, double key)
+{
+    uint32_t a = 0, b = n;
+    while (a < b) {
+        uint32_t mid = a + (b - a) / 2;
+        if (v[mid] < key) a = mid + 1; else b = mid;
+    }
+    return a;
+}
+
+/* number of v[] less than or equal to key */
+static uint32_t count_le(const float *v, uint32_t n, double key)
+{
+    uint32_t a = 0, b = n;
+    while (a < b) {
+        uint32_t mid = a + (b - a) / 2;
+        if (v[mid] <= key) a = mid + 1; else b = mid;
+    }
+    return a;
+}
+
+uint64_t oracle_bits_count(const float *upd_lo, const float *upd_hi, uint32_t m,
+                           const float *sub_lo, const float *sub_hi, uint32_t n,
+                           uint32_t *counts)
+{
+    float *bs = (float *)malloc((size_t)(n ? n : 1) * sizeof(float));
+    float *be = (float *)malloc((size_t)(n ? n : 1) * sizeof(float));
+    if (!bs || !be) { free(bs); free(be); return UINT64_MAX; }
+    memcpy(bs, sub_lo, (size_t)n * sizeof(float));
+    memcpy(be, sub_hi, (size_t)n * sizeof(float));
+    qsort(bs, n, sizeof(float), cmp_float);
+    qsort(be, n, sizeof(float), cmp_float);
+    uint64_t K = 0;
+    for (uint32_t j = 0; j < m; ++j) {
+        uint32_t end_before = count_less(be, n, upd_lo[j]);      /* S.hi < q.lo */
+        uint32_t start_after = n - count_le(bs, n, upd_hi[j]);   /* S.lo > q.hi */
+        uint32_t c = n - end_before - start_after;
+        if (counts) counts[j] = c;
+        K += c;
+    }
+    free(bs);
+    free(be);
+    return K;
+}
+
+int oracle_openmp_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
