@@ -1,0 +1,360 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of GPU interval tree matching (one JSON line).
+
+A step is one whole match of the workload: sort and tree build over the
+subscriptions (ddm_build), the counting pass and scan over all updates
+(ddm_plan), then the write pass in update ranges whose pairs fit the device
+pair buffer (ddm_chunk_end + ddm_write), every pair written to HBM.  Inputs
+(240 MB for the default workload) are larger than L2, so no flush is needed.
+
+Default workload: d = 3, 5e6 updates + 5e6 subscriptions, centres from 64
+Gaussian clusters, log-normal extents, overlap degree 100 (the N = 1e7,
+alpha = 100 stress case); about 4.4e10 pairs (354 GB), so the write pass
+runs in chunks.
+
+Reported: matched pairs/s (value) and update queries/s; p50/p99 step
+latency; the write-pass kernel against the measured HBM roofline; the same
+metric end to end with host buffers (inputs copied in, every pair copied
+out); the CPU oracle on a bounded sample of the same workload.
+
+``--impl reference`` times the CPU oracle (interval tree matching with
+OpenMP over queries on the host cores) on a bounded sample instead.
+Multi-GPU (torchrun): every rank matches its own update set (seed shifted by
+rank) against the same subscriptions; no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
+METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default=DEFAULT_CONFIG)
+    ap.add_argument("--chunk-gb", type=float, default=64.0, help="device pair buffer (GB)")
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--stage-gb", type=float, default=2.0, help="pinned host staging (GB)")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(name, rank):
+    from paper_1309_3458_gb300 import workloads as W
+    arrays = W.make(name)
+    if rank:
+        # a different update set per rank, same subscriptions
+        c = dict(W.CONFIGS[name])
+        shifted = (W.uniform_fixed_length(c["n"], c["m"], c["d"], c["alpha"], c["seed"] + rank)
+                   if c["kind"] == "uniform" else
+                   W.clustered_lognormal(c["n"], c["m"], c["d"], c["alpha"], c["seed"] + rank))
+        arrays = (shifted[0], shifted[1], arrays[2], arrays[3])
+    return arrays
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi during a region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc or not os.path.exists(self.path):
+            return None
+        mhz, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                mhz.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return None
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def cpu_oracle_sample(arrays, budget_s):
+    """Oracle ITM (all host cores) on a bounded sample of the workload: one
+    interval tree build over all subscriptions plus a random sample of the
+    updates; pairs/s extrapolated to the whole update set (one build, all
+    queries at the sampled rate)."""
+    import numpy as np
+
+    import oracle
+    ulo, uhi, slo, shi = arrays
+    m = ulo.shape[1]
+    threads = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(123)
+    sub = lambda idx: (np.ascontiguousarray(ulo[:, idx]), np.ascontiguousarray(uhi[:, idx]))
+    # probe: build + 256 queries, to size the sample
+    probe = np.sort(rng.choice(m, min(m, 256), replace=False))
+    tm = []
+    oracle.itm_count(*sub(probe), slo, shi, threads=threads, timings=tm)
+    t_build, per_q = tm[0], max(1e-7, tm[1] / len(probe))
+    q = int(min(m, max(256, (budget_s - t_build) / per_q)))
+    sample = np.sort(rng.choice(m, q, replace=False))
+    tm = []
+    t0 = time.perf_counter()
+    K, _, _ = oracle.itm_count(*sub(sample), slo, shi, threads=threads, timings=tm)
+    wall = time.perf_counter() - t0
+    t_build, t_q = tm
+    t_all = t_build + t_q * m / q
+    return {"value": K * m / q / t_all, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+            "sample": (f"interval tree (AVL) build over all {slo.shape[1]} subscriptions "
+                       f"({t_build:.2f} s) + {q} of {m} updates queried with OpenMP on "
+                       f"{threads} threads ({t_q:.2f} s, {K} pairs); rate extrapolated to all "
+                       f"updates"),
+            "queries_per_s": m / t_all, "seconds": wall}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return
+    arrays = workload(args.config, 0)
+    res = []
+    for _ in range(args.warmup + args.steps):
+        res.append(cpu_oracle_sample(arrays, args.cpu_seconds / max(1, args.steps)))
+    timed = res[args.warmup:]
+    v = statistics.mean(r["value"] for r in timed)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "pairs/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * statistics.mean(r["seconds"] for r in timed),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": {"workload": args.config},
+            "cpu_baseline": {"value": v, "unit": "pairs/s", "cores": timed[0]["cores"],
+                             "kind": "oracle", "sample": timed[0]["sample"]},
+            "e2e": {"value": v, "unit": "pairs/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist()
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as tdist
+
+    import paper_1309_3458_gb300 as ddm
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl")
+
+    def barrier():
+        if world > 1:
+            tdist.barrier()
+
+    arrays = workload(args.config, rank)
+    d, m = arrays[0].shape
+    n = arrays[2].shape[1]
+    dev = tuple(torch.from_numpy(a).cuda() for a in arrays)
+    ctx = ddm.ddm_create(local)
+    cap = int(args.chunk_gb * 1e9) // 8
+    pairs = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    write_ms, write_bytes = [], []
+
+    def step(record=False):
+        ddm.ddm_build(ctx, dev[2], dev[3])
+        K = ddm.ddm_plan(ctx, dev[0], dev[1])
+        b = 0
+        while b < m:
+            e = ddm.ddm_chunk_end(ctx, b, cap)
+            if record:
+                s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                s0.record(stream)
+            k = ddm.ddm_write(ctx, b, e, pairs)
+            if record:
+                s1.record(stream)
+                write_ms.append((s0, s1))
+                write_bytes.append(8 * d * (e - b) + 8 * d * n + 8 * k)
+            b = e
+        return K
+
+    K = 0
+    for _ in range(args.warmup):
+        K = step()
+    torch.cuda.synchronize()
+    barrier()
+    torch.cuda.synchronize()
+    l0 = ddm.ddm_debug_launch_count()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    with Clocks(local) as clk:
+        ev[0].record(stream)
+        for i in range(args.steps):
+            K = step(record=True)
+            ev[i + 1].record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = (ddm.ddm_debug_launch_count() - l0) // args.steps
+    total_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    t_local = total_ms / 1e3
+    pairs_local = K * args.steps
+    if world > 1:
+        tt = torch.tensor([t_local, float(pairs_local)], dtype=torch.float64, device="cuda")
+        mx = tt.clone()
+        tdist.all_reduce(mx[0:1], op=tdist.ReduceOp.MAX)
+        tdist.all_reduce(tt[1:2], op=tdist.ReduceOp.SUM)
+        t_job, pairs_job = float(mx[0]), float(tt[1])
+    else:
+        t_job, pairs_job = t_local, float(pairs_local)
+    wtimes = [a.elapsed_time(b) for a, b in write_ms]
+    write_s = sum(wtimes) / 1e3
+    write_gbs = sum(write_bytes) / write_s / 1e9 if write_s > 0 else 0.0
+
+    peaks = {}
+    if os.path.exists(PEAKS):
+        peaks = json.load(open(PEAKS))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+
+    # ---- end to end with host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        host = [torch.from_numpy(a).pin_memory() for a in arrays]
+        stage = torch.empty((int(args.stage_gb * 1e9) // 8, 2), dtype=torch.int32).pin_memory()
+        h2d = sum(a.nbytes for a in arrays)
+        e2e_steps = args.e2e_steps or max(1, min(args.steps, 3))
+
+        def e2e_step():
+            for t_dev, t_host in zip(dev, host):
+                t_dev.copy_(t_host, non_blocking=True)
+            ddm.ddm_build(ctx, dev[2], dev[3])
+            Ke = ddm.ddm_plan(ctx, dev[0], dev[1])
+            b = 0
+            while b < m:
+                e = ddm.ddm_chunk_end(ctx, b, cap)
+                k = ddm.ddm_write(ctx, b, e, pairs)
+                o = 0
+                while o < k:
+                    c = min(stage.shape[0], k - o)
+                    stage[:c].copy_(pairs[o:o + c], non_blocking=True)
+                    o += c
+                b = e
+            torch.cuda.synchronize()
+            return Ke
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(e2e_steps):
+            Ke = e2e_step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        te = e0.elapsed_time(e1) / 1e3
+        e2e = {"value": Ke * e2e_steps / te * (world if world > 1 else 1), "unit": "pairs/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * Ke),
+               "steps": e2e_steps}
+        del host, stage
+
+    ddm.ddm_destroy(ctx)
+    if rank != 0:
+        return
+
+    cpu = None
+    if not args.no_cpu and world == 1:
+        cpu = cpu_oracle_sample(arrays, args.cpu_seconds)
+        cpu.pop("seconds", None)
+
+    clocks = clk.summary()
+    line = {
+        "metric": METRIC,
+        "value": pairs_job / t_job,
+        "unit": "pairs/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": args.config, "d": d, "n_sub": n, "m_upd": m, "K": K,
+                   "chunk_pairs": cap, "l2": "inputs (%.0f MB) larger than L2" % (
+                       sum(a.nbytes for a in arrays) / 1e6)},
+        "queries_per_s": m * args.steps * world / t_job,
+        "p50_ms": float(np.percentile(step_ms, 50)),
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "roofline": {"bound": "hbm", "kernel": "k_packets<write> (ddm_write)",
+                     "achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": write_gbs / hbm_peak, "traffic": None,
+                     "peak_source": peak_src,
+                     "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 8*(pairs in chunk)",
+                     "write_ms_per_step": 1e3 * write_s / args.steps},
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "cpu_baseline": cpu,
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * ddm.h -- C ABI of libddm, GPU interval tree matching for Data Distribution
+ * Management (Marzolla, D'Angelo, Mandrioli, "A Parallel Data Distribution
+ * Management Algorithm", DS-RT 2013).
+ *
+ * Problem (Section III): given subscription extents S_0..S_{n-1} and update
+ * extents U_0..U_{m-1}, each a d-dimensional rectangle, report every pair
+ * (U_j, S_i) whose intersection is non-empty.  Two d-rectangles intersect
+ * iff their projections intersect in every dimension (Section III-A); the
+ * per-dimension test is Intersect-1D (Alg. 1).  Ids are the 0-based
+ * positions of the extents in their input arrays.
+ *
+ * Method (Section IV, Algs. 4 and 5): an interval tree is built over the
+ * subscriptions, ordered by dimension-0 lower bound (ties by upper bound,
+ * then id) with the maximum upper bound and minimum lower bound kept per
+ * subtree; every update runs one overlap query against it, testing every
+ * dimension with Intersect-1D.  On the GPU the tree is implicit (32 children
+ * per node), keeps the subtree bounds for every dimension, and refines the
+ * order near the leaves by the lower bounds of dimensions 1..d-1 inside
+ * aligned groups of the dimension-0 order.  Queries are independent
+ * (Section IV, "Parallelizing ITM") and run 32 per warp.
+ *
+ * Conventions shared by every call:
+ *  - Coordinates are float32 in structure-of-arrays layout: for a set of c
+ *    extents, lo[k*c + i] / hi[k*c + i] are the lower / upper bound of
+ *    extent i in dimension k (0 <= k < d).  Input pointers are DEVICE
+ *    pointers (memory of the context's device), read only, owned by the
+ *    caller, and must stay valid and unchanged until the call returns (for
+ *    the staged calls: until the last call that uses them).
+ *  - Every extent must satisfy lo <= hi in every dimension and contain no
+ *    NaN; +-inf is allowed.  A violation gives DDM_ERR_EXTENT.
+ *  - `stream` is a cudaStream_t (NULL = the legacy default stream).  All GPU
+ *    work is enqueued on it in order.  Calls that return a count (k_out)
+ *    synchronise `stream` once to read it; nothing else blocks the host.
+ *  - Output pairs are written to caller-owned DEVICE memory.  Order: update
+ *    id ascending, then the subscriptions' position in the tree (for d = 1
+ *    that is dimension-0 lower, upper, id).  Only the set of pairs is the
+ *    result; the order is deterministic for a given input.
+ *  - Sizes: 1 <= d <= DDM_MAX_DIMS, n and m <= DDM_MAX_EXTENTS; n == 0 or
+ *    m == 0 is valid and gives K = 0.
+ *  - A context is not thread safe: one host thread at a time per context.
+ */
+#ifndef DDM_H
+#define DDM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return codes. */
+#define DDM_OK            0
+#define DDM_ERR_ARG       1  /* null pointer, d out of range, size too large, bad range */
+#define DDM_ERR_EXTENT    2  /* an extent has lo > hi or a NaN coordinate */
+#define DDM_ERR_CAPACITY  3  /* more pairs than `capacity`; *k_out holds the needed count */
+#define DDM_ERR_NOMEM     4  /* device workspace allocation failed */
+#define DDM_ERR_CUDA      5  /* a CUDA runtime call or kernel launch failed */
+#define DDM_ERR_TIMEOUT   6  /* a bounded device-side wait gave up */
+#define DDM_ERR_STATE     7  /* staged call without the build / plan it needs */
+
+/* Flags. */
+#define DDM_CLOSED 0u  /* default: closed segments, x.lo <= y.hi && y.lo <= x.hi */
+#define DDM_OPEN   1u  /* Alg. 1 as printed: x.lo < y.hi && y.lo < x.hi */
+
+#define DDM_MAX_DIMS    8
+#define DDM_MAX_EXTENTS 1073741823u  /* 2^30 - 1 per set */
+
+/* One intersecting pair: update id and subscription id (0-based). */
+typedef struct {
+    uint32_t upd;
+    uint32_t sub;
+} ddm_pair;
+
+/* Opaque context: owns the device workspace (sort buffers, the tree, the
+ * per-update plan) on one device.  Grows on demand, freed by ddm_destroy. */
+typedef struct ddm_ctx ddm_ctx;
+
+/* Create a context on CUDA device `device`.  *ctx is set on success.
+ * Errors: DDM_ERR_ARG (ctx NULL), DDM_ERR_CUDA (no such device),
+ * DDM_ERR_NOMEM. */
+int ddm_create(ddm_ctx **ctx, int device);
+
+/* Free a context and its device workspace (NULL is a no-op).  Waits for
+ * work the context enqueued to finish. */
+int ddm_destroy(ddm_ctx *ctx);
+
+/* Static description of a return code (never NULL). */
+const char *ddm_strerror(int code);
+
+/* ---------------------------------------------------------------------- */
+/* One-shot calls                                                          */
+/* ---------------------------------------------------------------------- */
+
+/* K = number of intersecting (update, subscription) pairs
+ * (Section III problem statement; Algs. 4-5 with the d-dimensional test of
+ * Section III-A).  Runs validation, the sort and tree build over S, and one
+ * counting query per update.  *k_out = K.  Synchronises `stream`.
+ * Errors: DDM_ERR_ARG, DDM_ERR_EXTENT, DDM_ERR_NOMEM, DDM_ERR_CUDA,
+ * DDM_ERR_TIMEOUT.  Leaves the tree and the plan in the context, as
+ * ddm_build + ddm_plan would. */
+int ddm_count(ddm_ctx *ctx, int d,
+              const float *upd_lo, const float *upd_hi, uint32_t m,
+              const float *sub_lo, const float *sub_hi, uint32_t n,
+              uint32_t flags, uint64_t *k_out, void *stream);
+
+/* Enumerate all K pairs into pairs[0..K) (device memory, capacity entries).
+ * *k_out = K.  If K > capacity: returns DDM_ERR_CAPACITY, *k_out = K and
+ * the contents of `pairs` are unspecified (nothing is written past
+ * capacity).  The intersection matrix M of Section III is returned in
+ * this compressed (coordinate list) form.  Synchronises `stream` once. */
+int ddm_match(ddm_ctx *ctx, int d,
+              const float *upd_lo, const float *upd_hi, uint32_t m,
+              const float *sub_lo, const float *sub_hi, uint32_t n,
+              uint32_t flags, ddm_pair *pairs, uint64_t capacity,
+              uint64_t *k_out, void *stream);
+
+/* As ddm_match, but only for updates upd_begin <= j < upd_end (ids stay
+ * global).  For outputs larger than device memory, call repeatedly over
+ * consecutive ranges, or use the staged calls below, which avoid redoing
+ * the tree.  Errors as ddm_match, plus DDM_ERR_ARG when the range is not
+ * within [0, m]. */
+int ddm_match_range(ddm_ctx *ctx, int d,
+                    const float *upd_lo, const float *upd_hi, uint32_t m,
+                    const float *sub_lo, const float *sub_hi, uint32_t n,
+                    uint32_t upd_begin, uint32_t upd_end,
+                    uint32_t flags, ddm_pair *pairs, uint64_t capacity,
+                    uint64_t *k_out, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Staged calls: resident tree, per-update plan, chunked output            */
+/* ---------------------------------------------------------------------- */
+
+/* Interval-Tree-Create (Alg. 5, Section IV) over the subscriptions:
+ * validates S, sorts it by dimension-0 (lower, upper, id) and builds the
+ * tree in the context, replacing any previous tree and plan.  The
+ * coordinates are copied, so sub_lo / sub_hi may be released afterwards.
+ * Synchronises `stream` (to report DDM_ERR_EXTENT). */
+int ddm_build(ddm_ctx *ctx, int d, const float *sub_lo, const float *sub_hi,
+              uint32_t n, void *stream);
+
+/* Counting pass (Alg. 4 per update, without output) for all m updates
+ * against the built tree, and the exclusive prefix sum of the per-update
+ * counts.  offsets (optional, device, m + 1 entries of uint64) receives the
+ * prefix: update j's pairs are [offsets[j], offsets[j+1]) of the full
+ * output, offsets[m] = K.  *k_out = K.  The context keeps the plan (with its
+ * own sorted copy of the update coordinates) for ddm_write /
+ * ddm_chunk_end, so upd_lo / upd_hi may be released afterwards.  Synchronises
+ * `stream`.  Errors: DDM_ERR_STATE (no tree), DDM_ERR_ARG, DDM_ERR_EXTENT,
+ * DDM_ERR_NOMEM, DDM_ERR_CUDA, DDM_ERR_TIMEOUT. */
+int ddm_plan(ddm_ctx *ctx, const float *upd_lo, const float *upd_hi, uint32_t m,
+             uint32_t flags, uint64_t *offsets, uint64_t *k_out, void *stream);
+
+/* Write the pairs of updates upd_begin <= j < upd_end of the current plan
+ * into pairs[0 .. offsets[upd_end] - offsets[upd_begin]).  *k_out = that
+ * count.  DDM_ERR_CAPACITY (nothing written) if it exceeds capacity.
+ * Synchronises `stream`.  Errors: DDM_ERR_STATE (no plan), DDM_ERR_ARG,
+ * DDM_ERR_CAPACITY, DDM_ERR_CUDA. */
+int ddm_write(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end,
+              ddm_pair *pairs, uint64_t capacity, uint64_t *k_out, void *stream);
+
+/* Chunk planning for ddm_write: *upd_end = the largest e <= m such that
+ * the pairs of updates [upd_begin, e) fit in `capacity`.  Returns
+ * DDM_ERR_CAPACITY with *upd_end = upd_begin when update upd_begin alone
+ * does not fit.  Synchronises `stream`. */
+int ddm_chunk_end(ddm_ctx *ctx, uint32_t upd_begin, uint64_t capacity,
+                  uint32_t *upd_end, void *stream);
+
+/* ---------------------------------------------------------------------- */
+/* Introspection of the built tree (for checking intermediate results)     */
+/* ---------------------------------------------------------------------- */
+
+/* Shape of the implicit tree: *levels = number of internal levels L;
+ * counts[l-1] (l = 1..L, at most DDM_MAX_TREE_LEVELS entries) = nodes at
+ * level l.  Level-l node g covers the sorted positions
+ * [g * 32^l, min(n, (g+1) * 32^l)).  *total = sum of counts. */
+#define DDM_MAX_TREE_LEVELS 8
+int ddm_tree_shape(ddm_ctx *ctx, int *levels, uint32_t *counts, uint32_t *total);
+
+/* Copy the tree to caller device memory (any pointer may be NULL):
+ *  order[n]         -- subscription id at each sorted position (tree order);
+ *  node_lo[d*total] -- per dimension k and node, the minimum lower bound of
+ *                      the node's range (minlower of Section IV);
+ *  node_hi[d*total] -- per dimension k and node, the maximum upper bound of
+ *                      the node's range (maxupper of Section IV);
+ * entry [k*total + j]: nodes are stored level by level from level 1, in
+ * node order, so level l starts at sum of counts[0..l-2].
+ * Enqueued on `stream`; no synchronisation.  DDM_ERR_STATE without a tree. */
+int ddm_tree_export(ddm_ctx *ctx, uint32_t *order, float *node_lo, float *node_hi,
+                    void *stream);
+
+/* Testing aid: make device workspace allocations that would bring the
+ * context's total above `bytes` fail with DDM_ERR_NOMEM (0 = no limit). */
+int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);
+
+/* Number of CUDA kernels this library has launched in the calling process
+ * since it was loaded (all contexts).  Host-side counter, no GPU access. */
+uint64_t ddm_debug_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDM_H */

@@ -64,7 +64,8 @@ def bind(cdll):
                             ctypes.c_uint32, u32, u64, u32, u32, ctypes.c_uint64]
     L.oracle_itm_count.restype = ctypes.c_uint64
     L.oracle_itm_count.argtypes = [ctypes.c_int, f32, f32, ctypes.c_uint32, f32, f32,
-                                   ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, u32, u64]
+                                   ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int, u32, u64,
+                                   ctypes.POINTER(ctypes.c_double)]
     L.oracle_itm_pairs.restype = ctypes.c_uint64
     L.oracle_itm_pairs.argtypes = [ctypes.c_int, f32, f32, ctypes.c_uint32, f32, f32,
                                    ctypes.c_uint32, ctypes.c_uint32, u32, u32, ctypes.c_uint64]
@@ -136,15 +137,20 @@ def bf(upd_lo, upd_hi, sub_lo, sub_hi, flags: int = 0, pairs: bool = True):
     return K, counts, digests, None, None
 
 
-def itm_count(upd_lo, upd_hi, sub_lo, sub_hi, flags: int = 0, threads: int = 1):
-    """Interval tree matching; returns ``(K, counts[m], digests[m])``."""
+def itm_count(upd_lo, upd_hi, sub_lo, sub_hi, flags: int = 0, threads: int = 1,
+              timings: Optional[list] = None):
+    """Interval tree matching; returns ``(K, counts[m], digests[m])``.  If
+    ``timings`` is a list, the build and query wall times (s) are appended."""
     d, m, n = _shape(upd_lo, upd_hi, sub_lo, sub_hi)
     counts = np.zeros(m, np.uint32)
     digests = np.zeros(m, np.uint64)
+    sec = (ctypes.c_double * 2)()
     K = int(lib().oracle_itm_count(d, _f32(upd_lo), _f32(upd_hi), m, _f32(sub_lo), _f32(sub_hi),
-                                   n, flags, threads, _u32(counts), _u64(digests)))
+                                   n, flags, threads, _u32(counts), _u64(digests), sec))
     if K == 2 ** 64 - 1:
         raise MemoryError("oracle tree allocation failed")
+    if timings is not None:
+        timings.extend([sec[0], sec[1]])
     return K, counts, digests
 
 

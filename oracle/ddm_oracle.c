@@ -33,9 +33,11 @@
  * closed-form lattice counts, against the worked example of Fig. 1 and
  * against BITS counting (Section II) by the CPU test suite.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -269,17 +271,28 @@ static void it_query_rec(const it_tree *t, int32_t x, it_query *q)
         it_query_rec(t, p->right, q);
 }
 
+static double now_s(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return ts.tv_sec + 1e-9 * ts.tv_nsec;
+}
+
 /* IntTree-Matching (Alg. 5) with per-update counts and digests; the loop
  * over updates is split across threads as in the paper's parallel ITM
- * (Section IV, "Parallelizing ITM"): every query only reads the tree. */
+ * (Section IV, "Parallelizing ITM"): every query only reads the tree.
+ * seconds (optional, 2 entries) receives the wall time of the tree build
+ * and of the queries. */
 uint64_t oracle_itm_count(int d,
                           const float *upd_lo, const float *upd_hi, uint32_t m,
                           const float *sub_lo, const float *sub_hi, uint32_t n,
                           uint32_t flags, int nthreads,
-                          uint32_t *counts, uint64_t *digests)
+                          uint32_t *counts, uint64_t *digests, double *seconds)
 {
     it_tree t;
+    double t0 = now_s();
     if (it_create(&t, sub_lo, sub_hi, n) != 0) return UINT64_MAX;
+    double t1 = now_s();
     uint64_t K = 0;
 #ifdef _OPENMP
     if (nthreads < 1) nthreads = 1;
@@ -295,6 +308,10 @@ uint64_t oracle_itm_count(int d,
         if (counts) counts[jj] = q.count;
         if (digests) digests[jj] = q.digest;
         K += q.count;
+    }
+    if (seconds) {
+        seconds[0] = t1 - t0;
+        seconds[1] = now_s() - t1;
     }
     free(t.v);
     return K;

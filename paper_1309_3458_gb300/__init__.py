@@ -1,0 +1,217 @@
+"""GPU interval tree matching for Data Distribution Management.
+
+Thin Python binding of ``libddm.so`` (C ABI declared in ``include/ddm.h``).
+Functions carry the C names and only marshal arguments: device tensors are
+passed as raw pointers, the stream is torch's current CUDA stream unless one
+is given.  Every step of the matching runs in the library's CUDA kernels;
+there is no CPU fallback, and importing a function fails loudly when the
+library has not been built (``python -m paper_1309_3458_gb300.build``).
+
+Array conventions (see ``include/ddm.h``): coordinates are float32 device
+tensors of shape ``(d, count)`` (row k = dimension k), C-contiguous.  The pair
+output is an int32 device tensor of shape ``(capacity, 2)``: column 0 the
+update id, column 1 the subscription id.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence, Tuple
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libddm.so")
+
+DDM_OK = 0
+DDM_ERR_ARG = 1
+DDM_ERR_EXTENT = 2
+DDM_ERR_CAPACITY = 3
+DDM_ERR_NOMEM = 4
+DDM_ERR_CUDA = 5
+DDM_ERR_TIMEOUT = 6
+DDM_ERR_STATE = 7
+
+DDM_CLOSED = 0
+DDM_OPEN = 1
+DDM_MAX_DIMS = 8
+DDM_MAX_EXTENTS = (1 << 30) - 1
+DDM_MAX_TREE_LEVELS = 8
+
+# Every entry point declared in include/ddm.h, with its ctypes signature.
+_vp, _i, _u32, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
+_pu32, _pu64, _pi = (ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_uint64),
+                     ctypes.POINTER(ctypes.c_int))
+_SET = [_vp, _vp, _u32]  # lo, hi, count
+SIGNATURES = {
+    "ddm_create": (_i, [ctypes.POINTER(_vp), _i]),
+    "ddm_destroy": (_i, [_vp]),
+    "ddm_strerror": (ctypes.c_char_p, [_i]),
+    "ddm_count": (_i, [_vp, _i] + _SET + _SET + [_u32, _pu64, _vp]),
+    "ddm_match": (_i, [_vp, _i] + _SET + _SET + [_u32, _vp, _u64, _pu64, _vp]),
+    "ddm_match_range": (_i, [_vp, _i] + _SET + _SET + [_u32, _u32, _u32, _vp, _u64, _pu64, _vp]),
+    "ddm_build": (_i, [_vp, _i, _vp, _vp, _u32, _vp]),
+    "ddm_plan": (_i, [_vp, _vp, _vp, _u32, _u32, _vp, _pu64, _vp]),
+    "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
+    "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
+    "ddm_tree_shape": (_i, [_vp, _pi, _pu32, _pu32]),
+    "ddm_tree_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "ddm_debug_set_alloc_limit": (_i, [_vp, _u64]),
+    "ddm_debug_launch_count": (_u64, []),
+}
+
+_lib = None
+
+
+class DDMError(RuntimeError):
+    """Non-zero return code of a libddm call; ``k`` holds *k_out when set."""
+
+    def __init__(self, code: int, where: str, k: Optional[int] = None):
+        self.code = code
+        self.k = k
+        super().__init__(f"{where}: {ddm_strerror(code)} (code {code})")
+
+
+def lib():
+    """Load libddm.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} missing: build it with "
+                               "`python -m paper_1309_3458_gb300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def ddm_strerror(code: int) -> str:
+    return lib().ddm_strerror(code).decode()
+
+
+def _ptr(t) -> Optional[int]:
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> Optional[int]:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _set(lo, hi) -> Tuple[int, int, int, int]:
+    d, c = lo.shape
+    assert hi.shape == lo.shape, "lo and hi must have the same shape"
+    assert lo.is_contiguous() and hi.is_contiguous(), "coordinates must be C-contiguous"
+    return d, _ptr(lo), _ptr(hi), c
+
+
+def _check(rc: int, where: str, k: Optional[int] = None):
+    if rc != DDM_OK:
+        raise DDMError(rc, where, k)
+
+
+def ddm_create(device: int = 0) -> int:
+    h = ctypes.c_void_p()
+    _check(lib().ddm_create(ctypes.byref(h), device), "ddm_create")
+    return h.value
+
+
+def ddm_destroy(ctx: int) -> None:
+    _check(lib().ddm_destroy(ctx), "ddm_destroy")
+
+
+def ddm_count(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, flags: int = DDM_CLOSED,
+              stream=None) -> int:
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d2, sl, sh, n = _set(sub_lo, sub_hi)
+    assert d == d2
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_count(ctx, d, ul, uh, m, sl, sh, n, flags, ctypes.byref(k), _stream(stream))
+    _check(rc, "ddm_count", k.value)
+    return k.value
+
+
+def ddm_match(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, pairs, flags: int = DDM_CLOSED,
+              stream=None) -> int:
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d2, sl, sh, n = _set(sub_lo, sub_hi)
+    assert d == d2
+    cap = 0 if pairs is None else pairs.shape[0]
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_match(ctx, d, ul, uh, m, sl, sh, n, flags, _ptr(pairs), cap, ctypes.byref(k),
+                         _stream(stream))
+    _check(rc, "ddm_match", k.value)
+    return k.value
+
+
+def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, upd_end: int,
+                    pairs, flags: int = DDM_CLOSED, stream=None) -> int:
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d2, sl, sh, n = _set(sub_lo, sub_hi)
+    assert d == d2
+    cap = 0 if pairs is None else pairs.shape[0]
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_match_range(ctx, d, ul, uh, m, sl, sh, n, upd_begin, upd_end, flags,
+                               _ptr(pairs), cap, ctypes.byref(k), _stream(stream))
+    _check(rc, "ddm_match_range", k.value)
+    return k.value
+
+
+def ddm_build(ctx: int, sub_lo, sub_hi, stream=None) -> None:
+    d, sl, sh, n = _set(sub_lo, sub_hi)
+    _check(lib().ddm_build(ctx, d, sl, sh, n, _stream(stream)), "ddm_build")
+
+
+def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
+             stream=None) -> int:
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_plan(ctx, ul, uh, m, flags, _ptr(offsets), ctypes.byref(k), _stream(stream))
+    _check(rc, "ddm_plan", k.value)
+    return k.value
+
+
+def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int:
+    cap = 0 if pairs is None else pairs.shape[0]
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_write(ctx, upd_begin, upd_end, _ptr(pairs), cap, ctypes.byref(k),
+                         _stream(stream))
+    _check(rc, "ddm_write", k.value)
+    return k.value
+
+
+def ddm_chunk_end(ctx: int, upd_begin: int, capacity: int, stream=None) -> int:
+    e = ctypes.c_uint32(0)
+    rc = lib().ddm_chunk_end(ctx, upd_begin, capacity, ctypes.byref(e), _stream(stream))
+    _check(rc, "ddm_chunk_end", e.value)
+    return e.value
+
+
+def ddm_tree_shape(ctx: int) -> Tuple[int, Sequence[int], int]:
+    lv = ctypes.c_int(0)
+    cnt = (ctypes.c_uint32 * DDM_MAX_TREE_LEVELS)()
+    tot = ctypes.c_uint32(0)
+    _check(lib().ddm_tree_shape(ctx, ctypes.byref(lv), cnt, ctypes.byref(tot)), "ddm_tree_shape")
+    return lv.value, list(cnt)[: lv.value], tot.value
+
+
+def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=None) -> None:
+    _check(lib().ddm_tree_export(ctx, _ptr(order), _ptr(node_lo), _ptr(node_hi),
+                                 _stream(stream)), "ddm_tree_export")
+
+
+def ddm_debug_set_alloc_limit(ctx: int, nbytes: int) -> None:
+    _check(lib().ddm_debug_set_alloc_limit(ctx, nbytes), "ddm_debug_set_alloc_limit")
+
+
+def ddm_debug_launch_count() -> int:
+    return int(lib().ddm_debug_launch_count())

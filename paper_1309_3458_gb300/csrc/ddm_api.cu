@@ -1,0 +1,491 @@
+// Host side of the C ABI (include/ddm.h): argument checks, device workspace,
+// stream-ordered launches and the single status read-back per call.
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+#include "ddm_internal.cuh"
+
+using namespace ddm;
+
+namespace {
+std::atomic<unsigned long long> g_launches{0};
+}  // namespace
+
+void ddm::note_launches(unsigned count) { g_launches.fetch_add(count, std::memory_order_relaxed); }
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+};
+
+}  // namespace
+
+struct ddm_ctx {
+  int device = 0;
+  int sms = 0;
+  uint64_t alloc_limit = 0;  // 0 = unlimited (testing aid)
+  uint64_t allocated = 0;
+
+  Status* st_dev = nullptr;
+  Status* st_host = nullptr;  // pinned mirror
+
+  // sort scratch (shared by the subscription and the update sorts)
+  DevBuf keys[2], vals[2], hist, lookback, counters;
+  // tree
+  DevBuf e, sid, nodes;
+  // plan: sorted updates, per-update counts and offsets
+  DevBuf qe, qid, counts, offsets, sums, work;
+  // range selection for ddm_write over a sub-range of updates
+  DevBuf sel_offs, sel_list;
+
+  bool built = false;
+  TreeView tree{};
+  bool planned = false;
+  const float* ulo = nullptr;
+  const float* uhi = nullptr;
+  uint32_t m = 0;
+  uint32_t flags = 0;
+};
+
+namespace {
+
+class DeviceGuard {
+ public:
+  explicit DeviceGuard(int dev) {
+    ok_ = cudaGetDevice(&prev_) == cudaSuccess;
+    if (ok_ && prev_ != dev) ok_ = cudaSetDevice(dev) == cudaSuccess;
+    switched_ = ok_ && prev_ != dev;
+  }
+  ~DeviceGuard() {
+    if (switched_) cudaSetDevice(prev_);
+  }
+  bool ok() const { return ok_; }
+
+ private:
+  int prev_ = 0;
+  bool ok_ = false, switched_ = false;
+};
+
+int ensure(ddm_ctx* c, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return DDM_OK;
+  size_t want = bytes + bytes / 4;  // headroom against regrowth
+  if (b.p) {
+    cudaFree(b.p);
+    c->allocated -= b.cap;
+    b.p = nullptr;
+    b.cap = 0;
+  }
+  if (c->alloc_limit && c->allocated + want > c->alloc_limit) {
+    want = bytes;
+    if (c->allocated + want > c->alloc_limit) return DDM_ERR_NOMEM;
+  }
+  if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    cudaGetLastError();  // clear the sticky-free allocation error
+    b.p = nullptr;
+    return DDM_ERR_NOMEM;
+  }
+  b.cap = want;
+  c->allocated += want;
+  return DDM_OK;
+}
+
+void release(DevBuf& b) {
+  if (b.p) cudaFree(b.p);
+  b.p = nullptr;
+  b.cap = 0;
+}
+
+#define DDM_TRY(expr)              \
+  do {                             \
+    int rc_ = (expr);              \
+    if (rc_ != DDM_OK) return rc_; \
+  } while (0)
+#define DDM_CUDA(expr)                    \
+  do {                                    \
+    if ((expr) != cudaSuccess) {          \
+      cudaGetLastError();                 \
+      return DDM_ERR_CUDA;                \
+    }                                     \
+  } while (0)
+
+bool set_ok(int d, const float* lo, const float* hi, uint32_t cnt) {
+  if (cnt > DDM_MAX_EXTENTS) return false;
+  if (cnt > 0 && (!lo || !hi)) return false;
+  (void)d;
+  return true;
+}
+
+int sync_status(ddm_ctx* c, cudaStream_t s) {
+  DDM_CUDA(cudaMemcpyAsync(c->st_host, c->st_dev, sizeof(Status), cudaMemcpyDeviceToHost, s));
+  DDM_CUDA(cudaStreamSynchronize(s));
+  return DDM_OK;
+}
+
+int status_code(const Status& st) {
+  if (st.err & kErrTimeout) return DDM_ERR_TIMEOUT;
+  if (st.err & kErrExtent) return DDM_ERR_EXTENT;
+  if (st.err & kErrCapacity) return DDM_ERR_CAPACITY;
+  return DDM_OK;
+}
+
+int ensure_sort(ddm_ctx* c, uint32_t cnt) {
+  DDM_TRY(ensure(c, c->keys[0], sizeof(unsigned long long) * cnt));
+  DDM_TRY(ensure(c, c->keys[1], sizeof(unsigned long long) * cnt));
+  DDM_TRY(ensure(c, c->vals[0], sizeof(uint32_t) * cnt));
+  DDM_TRY(ensure(c, c->vals[1], sizeof(uint32_t) * cnt));
+  DDM_TRY(ensure(c, c->hist, sizeof(uint32_t) * 8 * 256));
+  DDM_TRY(ensure(c, c->counters, sizeof(uint32_t) * 8));
+  DDM_TRY(ensure(c, c->lookback, sizeof(uint32_t) * sort_lookback_words(cnt)));
+  return DDM_OK;
+}
+
+// Radix sort of the keys/ids in buffer pair `cur` over `passes` 8-bit
+// digits; `cur` is updated to the buffer pair holding the result.
+int sort_pass(ddm_ctx* c, uint32_t cnt, int passes, int* cur, cudaStream_t s) {
+  SortScratch sc;
+  sc.keys[0] = static_cast<unsigned long long*>(c->keys[*cur].p);
+  sc.keys[1] = static_cast<unsigned long long*>(c->keys[*cur ^ 1].p);
+  sc.vals[0] = static_cast<uint32_t*>(c->vals[*cur].p);
+  sc.vals[1] = static_cast<uint32_t*>(c->vals[*cur ^ 1].p);
+  sc.hist = static_cast<uint32_t*>(c->hist.p);
+  sc.lookback = static_cast<uint32_t*>(c->lookback.p);
+  sc.counters = static_cast<uint32_t*>(c->counters.p);
+  int out = 0;
+  DDM_CUDA(launch_sort64(sc, cnt, passes, &out, c->st_dev, c->sms, s));
+  *cur ^= out;
+  return DDM_OK;
+}
+
+// Sort a set into the spatial order used by the tree: dimension-0 key first,
+// then, for each further dimension with a group size, a stable re-sort by
+// that dimension's lower bound inside aligned groups.  Validates the set on
+// the way.  Returns the buffer pair whose vals hold the order.
+int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt, bool tree,
+              int* cur, cudaStream_t s) {
+  *cur = 0;
+  DDM_TRY(ensure_sort(c, cnt));
+  DDM_CUDA(launch_validate(d, lo, hi, cnt, static_cast<unsigned long long*>(c->keys[0].p),
+                           static_cast<uint32_t*>(c->vals[0].p), tree ? 1 : 2, c->st_dev, c->sms,
+                           s));
+  DDM_TRY(sort_pass(c, cnt, tree ? 8 : 4, cur, s));
+  int glog2[DDM_MAX_DIMS];
+  str_groups(cnt, d, glog2);
+  for (int k = 1; k < d; ++k) {
+    if (!glog2[k]) continue;
+    DDM_CUDA(launch_rekey(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt, cnt,
+                          glog2[k], static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
+    int gbits = 0;
+    while (gbits < 32 && (((uint64_t)(cnt - 1) >> glog2[k]) >> gbits) != 0) ++gbits;
+    DDM_TRY(sort_pass(c, cnt, 4 + (gbits + 7) / 8, cur, s));
+  }
+  return DDM_OK;
+}
+
+// Validate S, sort it into tree order and build the tree (steps run on `s`,
+// no host synchronisation).
+int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n, cudaStream_t s) {
+  c->built = false;
+  c->planned = false;
+  TreeView t{};
+  t.d = d;
+  t.n = n;
+  if (n == 0) {
+    c->tree = t;
+    c->built = true;
+    return DDM_OK;
+  }
+  tree_shape(n, &t.L, t.cnt, t.off, &t.total);
+  DDM_TRY(ensure(c, c->e, sizeof(float2) * (size_t)d * n));
+  DDM_TRY(ensure(c, c->sid, sizeof(uint32_t) * n));
+  DDM_TRY(ensure(c, c->nodes, sizeof(float2) * (size_t)d * t.total));
+  int cur = 0;
+  DDM_TRY(order_set(c, d, slo, shi, n, true, &cur, s));
+  t.e = static_cast<const float2*>(c->e.p);
+  t.sid = static_cast<const uint32_t*>(c->sid.p);
+  t.nodes = static_cast<const float2*>(c->nodes.p);
+  DDM_CUDA(launch_build(t, static_cast<const uint32_t*>(c->vals[cur].p), slo, shi,
+                        static_cast<float2*>(c->e.p), static_cast<uint32_t*>(c->sid.p),
+                        static_cast<float2*>(c->nodes.p), s));
+  c->tree = t;
+  c->built = true;
+  return DDM_OK;
+}
+
+QueryView query_view(ddm_ctx* c) {
+  QueryView q{};
+  q.m = c->m;
+  q.qe = static_cast<const float2*>(c->qe.p);
+  q.qid = static_cast<const uint32_t*>(c->qid.p);
+  q.list = nullptr;
+  q.nq = c->m;
+  return q;
+}
+
+// Validate U, sort it, count per update, scan (no host synchronisation).
+int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_t flags,
+               cudaStream_t s) {
+  c->planned = false;
+  const int d = c->tree.d;
+  DDM_TRY(ensure(c, c->counts, sizeof(uint32_t) * (m ? m : 1)));
+  DDM_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * ((size_t)m + 1)));
+  DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * ((size_t)m / kScanTile + 2)));
+  DDM_TRY(ensure(c, c->work, sizeof(uint32_t)));
+  DDM_TRY(ensure(c, c->qe, sizeof(float2) * (size_t)d * (m ? m : 1)));
+  DDM_TRY(ensure(c, c->qid, sizeof(uint32_t) * (m ? m : 1)));
+  auto* counts = static_cast<uint32_t*>(c->counts.p);
+  auto* offsets = static_cast<unsigned long long*>(c->offsets.p);
+  c->m = m;
+  if (m > 0) {
+    int cur = 0;
+    DDM_TRY(order_set(c, d, ulo, uhi, m, false, &cur, s));
+    DDM_CUDA(launch_gather(d, static_cast<const uint32_t*>(c->vals[cur].p), ulo, uhi, m,
+                           static_cast<float2*>(c->qe.p), static_cast<uint32_t*>(c->qid.p), c->sms,
+                           s));
+    if (c->tree.n > 0) {
+      DDM_CUDA(launch_count(c->tree, query_view(c), flags, counts,
+                            static_cast<uint32_t*>(c->work.p), c->sms, s));
+    } else {
+      DDM_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * m, s));
+    }
+  }
+  DDM_CUDA(launch_scan(counts, m, offsets, static_cast<unsigned long long*>(c->sums.p), c->st_dev, s));
+  c->ulo = ulo;
+  c->uhi = uhi;
+  c->flags = flags;
+  c->planned = true;
+  return DDM_OK;
+}
+
+int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
+                cudaStream_t s) {
+  if (end > begin && c->tree.n > 0) {
+    QueryView q = query_view(c);
+    if (begin != 0 || end != c->m) {
+      DDM_TRY(ensure(c, c->sel_offs, sizeof(unsigned long long) * ((size_t)c->m + 1)));
+      DDM_TRY(ensure(c, c->sel_list, sizeof(uint32_t) * c->m));
+      DDM_CUDA(launch_select(q.qid, c->m, begin, end, static_cast<uint32_t*>(c->counts.p),
+                             static_cast<unsigned long long*>(c->sel_offs.p),
+                             static_cast<unsigned long long*>(c->sums.p),
+                             static_cast<uint32_t*>(c->sel_list.p), c->st_dev, s));
+      q.list = static_cast<const uint32_t*>(c->sel_list.p);
+      q.nq = end - begin;
+    }
+    DDM_CUDA(launch_write(c->tree, q, c->flags, begin, end,
+                          static_cast<const unsigned long long*>(c->offsets.p), pairs, capacity,
+                          static_cast<uint32_t*>(c->work.p), c->st_dev, c->sms, s));
+  } else {
+    DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
+  }
+  return DDM_OK;
+}
+
+int reset_status(ddm_ctx* c, cudaStream_t s) {
+  DDM_CUDA(cudaMemsetAsync(c->st_dev, 0, sizeof(Status), s));
+  return DDM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ddm_strerror(int code) {
+  switch (code) {
+    case DDM_OK: return "success";
+    case DDM_ERR_ARG: return "invalid argument";
+    case DDM_ERR_EXTENT: return "invalid extent (lo > hi or NaN)";
+    case DDM_ERR_CAPACITY: return "pair buffer too small";
+    case DDM_ERR_NOMEM: return "device memory allocation failed";
+    case DDM_ERR_CUDA: return "CUDA error";
+    case DDM_ERR_TIMEOUT: return "bounded device wait timed out";
+    case DDM_ERR_STATE: return "tree or plan missing";
+    default: return "unknown error";
+  }
+}
+
+int ddm_create(ddm_ctx** out, int device) {
+  if (!out) return DDM_ERR_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return DDM_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  ddm_ctx* c = new (std::nothrow) ddm_ctx();
+  if (!c) return DDM_ERR_NOMEM;
+  c->device = device;
+  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaMalloc(&c->st_dev, sizeof(Status)) != cudaSuccess ||
+      cudaMallocHost(&c->st_host, sizeof(Status)) != cudaSuccess) {
+    cudaGetLastError();
+    ddm_destroy(c);
+    return DDM_ERR_NOMEM;
+  }
+  *out = c;
+  return DDM_OK;
+}
+
+int ddm_destroy(ddm_ctx* c) {
+  if (!c) return DDM_OK;
+  DeviceGuard g(c->device);
+  cudaDeviceSynchronize();
+  for (DevBuf* b : {&c->keys[0], &c->keys[1], &c->vals[0], &c->vals[1], &c->hist, &c->lookback,
+                    &c->counters, &c->e, &c->sid, &c->nodes, &c->qe, &c->qid, &c->counts,
+                    &c->offsets, &c->sums, &c->work, &c->sel_offs, &c->sel_list})
+    release(*b);
+  if (c->st_dev) cudaFree(c->st_dev);
+  if (c->st_host) cudaFreeHost(c->st_host);
+  delete c;
+  return DDM_OK;
+}
+
+uint64_t ddm_debug_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+int ddm_debug_set_alloc_limit(ddm_ctx* c, uint64_t bytes) {
+  if (!c) return DDM_ERR_ARG;
+  c->alloc_limit = bytes;
+  return DDM_OK;
+}
+
+int ddm_build(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n, void* stream) {
+  if (!c || d < 1 || d > DDM_MAX_DIMS || !set_ok(d, slo, shi, n)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(build_async(c, d, slo, shi, n, s));
+  DDM_TRY(sync_status(c, s));
+  const int rc = status_code(*c->st_host);
+  if (rc != DDM_OK) c->built = false;
+  return rc;
+}
+
+int ddm_plan(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_t flags,
+             uint64_t* offsets, uint64_t* k_out, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->built) return DDM_ERR_STATE;
+  if (!set_ok(c->tree.d, ulo, uhi, m) || (flags & ~DDM_OPEN)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags, s));
+  if (offsets)
+    DDM_CUDA(cudaMemcpyAsync(offsets, c->offsets.p, sizeof(unsigned long long) * ((size_t)m + 1),
+                             cudaMemcpyDeviceToDevice, s));
+  DDM_TRY(sync_status(c, s));
+  if (k_out) *k_out = c->st_host->K;
+  const int rc = status_code(*c->st_host);
+  if (rc != DDM_OK) c->planned = false;
+  return rc;
+}
+
+int ddm_write(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
+              uint64_t* k_out, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  if (begin > end || end > c->m || (end > begin && !pairs)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
+  DDM_TRY(sync_status(c, s));
+  if (k_out) *k_out = c->st_host->K;
+  return status_code(*c->st_host);
+}
+
+int ddm_chunk_end(ddm_ctx* c, uint32_t begin, uint64_t capacity, uint32_t* upd_end, void* stream) {
+  if (!c || !upd_end) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  if (begin > c->m) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_CUDA(launch_chunk_end(static_cast<const unsigned long long*>(c->offsets.p), c->m, begin,
+                            capacity, c->st_dev, s));
+  DDM_TRY(sync_status(c, s));
+  *upd_end = (uint32_t)c->st_host->aux;
+  if (*upd_end == begin && begin < c->m) return DDM_ERR_CAPACITY;
+  return DDM_OK;
+}
+
+static int match_impl(ddm_ctx* c, int d, const float* ulo, const float* uhi, uint32_t m,
+                      const float* slo, const float* shi, uint32_t n, uint32_t begin, uint32_t end,
+                      uint32_t flags, ddm_pair* pairs, uint64_t capacity, uint64_t* k_out,
+                      void* stream, bool write) {
+  if (!c || d < 1 || d > DDM_MAX_DIMS || !set_ok(d, ulo, uhi, m) || !set_ok(d, slo, shi, n) ||
+      (flags & ~DDM_OPEN) || begin > end || end > m)
+    return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(build_async(c, d, slo, shi, n, s));
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags, s));
+  if (write) {
+    if (end > begin && !pairs && capacity > 0) return DDM_ERR_ARG;
+    DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
+  }
+  DDM_TRY(sync_status(c, s));
+  if (k_out) *k_out = c->st_host->K;
+  const int rc = status_code(*c->st_host);
+  if (rc == DDM_ERR_EXTENT || rc == DDM_ERR_TIMEOUT) c->built = c->planned = false;
+  return rc;
+}
+
+int ddm_count(ddm_ctx* c, int d, const float* ulo, const float* uhi, uint32_t m, const float* slo,
+              const float* shi, uint32_t n, uint32_t flags, uint64_t* k_out, void* stream) {
+  return match_impl(c, d, ulo, uhi, m, slo, shi, n, 0, m, flags, nullptr, 0, k_out, stream, false);
+}
+
+int ddm_match(ddm_ctx* c, int d, const float* ulo, const float* uhi, uint32_t m, const float* slo,
+              const float* shi, uint32_t n, uint32_t flags, ddm_pair* pairs, uint64_t capacity,
+              uint64_t* k_out, void* stream) {
+  return match_impl(c, d, ulo, uhi, m, slo, shi, n, 0, m, flags, pairs, capacity, k_out, stream,
+                    true);
+}
+
+int ddm_match_range(ddm_ctx* c, int d, const float* ulo, const float* uhi, uint32_t m,
+                    const float* slo, const float* shi, uint32_t n, uint32_t begin, uint32_t end,
+                    uint32_t flags, ddm_pair* pairs, uint64_t capacity, uint64_t* k_out,
+                    void* stream) {
+  return match_impl(c, d, ulo, uhi, m, slo, shi, n, begin, end, flags, pairs, capacity, k_out,
+                    stream, true);
+}
+
+int ddm_tree_shape(ddm_ctx* c, int* levels, uint32_t* counts, uint32_t* total) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->built) return DDM_ERR_STATE;
+  const TreeView& t = c->tree;
+  const int L = t.n ? t.L : 0;
+  if (levels) *levels = L;
+  uint32_t tot = 0;
+  for (int l = 1; l <= L; ++l) {
+    if (counts) counts[l - 1] = t.cnt[l];
+    tot += t.cnt[l];
+  }
+  if (total) *total = tot;
+  return DDM_OK;
+}
+
+int ddm_tree_export(ddm_ctx* c, uint32_t* order, float* node_lo, float* node_hi, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->built) return DDM_ERR_STATE;
+  if (c->tree.n == 0) return DDM_OK;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (order)
+    DDM_CUDA(cudaMemcpyAsync(order, c->sid.p, sizeof(uint32_t) * c->tree.n,
+                             cudaMemcpyDeviceToDevice, s));
+  DDM_CUDA(launch_export_nodes(c->tree, node_lo, node_hi, s));
+  return DDM_OK;
+}
+
+}  // extern "C"

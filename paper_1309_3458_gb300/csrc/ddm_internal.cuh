@@ -1,0 +1,134 @@
+// Internal declarations shared by the libddm translation units.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "ddm.h"
+
+namespace ddm {
+
+// Tree fan-out: one warp lane per child, so a node's 32 children are tested
+// by one coalesced load and one ballot.
+constexpr int kFan = 32;
+constexpr int kLog2Fan = 5;
+constexpr int kMaxLevels = DDM_MAX_TREE_LEVELS;
+
+// Device error bits (Status::err).
+constexpr unsigned kErrExtent = 1u;
+constexpr unsigned kErrTimeout = 2u;
+constexpr unsigned kErrCapacity = 4u;
+
+// Device-resident status word read back once per synchronising call.
+struct Status {
+  unsigned long long K;    // pairs counted (plan) or written (write)
+  unsigned int err;        // kErr* bits
+  unsigned int pad;
+  unsigned long long aux;  // call-specific (chunk end, ...)
+};
+
+// Read-only view of a built tree, passed to kernels by value.
+//
+// Elements (the subscriptions) sit at sorted positions 0..n-1; a level-l
+// node g covers positions [g*32^l, min(n, (g+1)*32^l)) and stores, per
+// dimension k, (minlower, maxupper) of the extents in its range.
+struct TreeView {
+  int d;
+  uint32_t n;
+  int L;                          // internal levels 1..L; level L has <= 32 nodes
+  uint32_t cnt[kMaxLevels + 1];   // nodes per level (index 1..L)
+  uint32_t off[kMaxLevels + 1];   // first node of each level within one dimension
+  uint32_t total;                 // nodes per dimension
+  const float2* e;                // [d][n] (lo, hi) per dimension, sorted order
+  const uint32_t* sid;            // [n] subscription id per sorted position
+  const float2* nodes;            // [d][total] (minlower, maxupper) per dimension
+};
+
+// Read-only view of the planned updates (queries) in their sorted order.
+struct QueryView {
+  uint32_t m;
+  const float2* qe;               // [d][m] (lo, hi) per dimension, sorted order
+  const uint32_t* qid;            // [m] update id per sorted position
+  const uint32_t* list;           // optional subset of sorted positions (ranges)
+  uint32_t nq;                    // number of queries to run (m, or |list|)
+};
+
+// Order-preserving map from float to uint32 (IEEE order; -0 maps like +0).
+__host__ __device__ inline uint32_t float_key(float f) {
+#ifdef __CUDA_ARCH__
+  uint32_t b = __float_as_uint(f);
+#else
+  uint32_t b;
+  __builtin_memcpy(&b, &f, 4);
+#endif
+  if (b == 0x80000000u) b = 0u;
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+// Number of kernels this library has launched in the process (all
+// contexts), for launch accounting by callers; defined in ddm_api.cu.
+void note_launches(unsigned count);
+
+// ---- ddm_layout.cu --------------------------------------------------------
+// Validate a set (lo <= hi, no NaN in every dimension) and, when keys is
+// not null, emit the sort key with the identity payload: key_mode 1 gives
+// (key(lo0) << 32 | key(hi0)) (tree order), key_mode 2 gives key(lo0).
+cudaError_t launch_validate(int d, const float* lo, const float* hi, uint32_t cnt,
+                            unsigned long long* keys, uint32_t* vals, int key_mode, Status* st,
+                            int sms, cudaStream_t s);
+// keys[i] = (i >> glog2) << 32 | key(lo_k[vals[i]]): re-sort inside groups.
+cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, int glog2,
+                         unsigned long long* keys, int sms, cudaStream_t s);
+// qe[k][i] = (lo_k, hi_k)[vals[i]], qid[i] = vals[i].
+cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const float* hi,
+                          uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s);
+
+// ---- ddm_sort.cu ----------------------------------------------------------
+struct SortScratch {
+  unsigned long long* keys[2];
+  uint32_t* vals[2];
+  uint32_t* hist;       // [8][256]
+  uint32_t* lookback;   // [8][tiles][256]
+  uint32_t* counters;   // [8]
+};
+constexpr int kSortTile = 4096;
+size_t sort_lookback_words(uint32_t n);
+// Stable LSD onesweep radix sort on the low 8*passes bits of 64-bit keys,
+// with a uint32 payload.  Input in keys[0]/vals[0]; *out_buf receives the
+// index (0 or 1) of the buffers holding the result.
+cudaError_t launch_sort64(SortScratch sc, uint32_t n, int passes, int* out_buf, Status* st,
+                          int sms, cudaStream_t s);
+
+// ---- ddm_tree.cu ----------------------------------------------------------
+void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* total);
+// Group sizes (log2) of the per-dimension re-sorts: dimension k >= 1 is
+// re-sorted by lower bound inside aligned groups of 2^glog2[k] positions.
+void str_groups(uint32_t n, int d, int* glog2);
+cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
+                         const float* hi, float2* e, uint32_t* sid, float2* nodes,
+                         cudaStream_t s);
+cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s);
+
+// ---- ddm_query.cu ---------------------------------------------------------
+cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
+                         uint32_t* work, int sms, cudaStream_t s);
+cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t begin,
+                         uint32_t end, const unsigned long long* offsets, ddm_pair* pairs,
+                         unsigned long long capacity, uint32_t* work, Status* st, int sms,
+                         cudaStream_t s);
+
+// ---- ddm_scan.cu ----------------------------------------------------------
+constexpr int kScanTile = 4096;
+// offsets[0..m] = exclusive prefix of counts; offsets[m] and st->K = total.
+cudaError_t launch_scan(const uint32_t* counts, uint32_t m, unsigned long long* offsets,
+                        unsigned long long* block_sums, Status* st, cudaStream_t s);
+cudaError_t launch_chunk_end(const unsigned long long* offsets, uint32_t m, uint32_t begin,
+                             unsigned long long capacity, Status* st, cudaStream_t s);
+// list = sorted positions i (ascending) with begin <= qid[i] < end; uses
+// flags/offs/sums as scratch.
+cudaError_t launch_select(const uint32_t* qid, uint32_t m, uint32_t begin, uint32_t end,
+                          uint32_t* flags, unsigned long long* offs, unsigned long long* sums,
+                          uint32_t* list, Status* st, cudaStream_t s);
+
+}  // namespace ddm

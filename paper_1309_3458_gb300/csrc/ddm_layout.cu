@@ -1,0 +1,102 @@
+// Input validation, sort keys and gathers of the structure-of-arrays layout.
+//
+// Every extent must have lo <= hi with no NaN in every dimension (the
+// paper's segments [low, high], Section III-A); a violation raises
+// kErrExtent.  For the subscription set the same pass emits the 64-bit sort
+// key of the interval tree order of Section IV -- lower bound, ties broken
+// by upper bound -- as (key(lo0) << 32 | key(hi0)), and the identity id
+// payload, so a stable radix sort leaves remaining ties in id order.  The
+// update set only needs a locality order: its key is key(lo0) alone.
+//
+// For d > 1 the order is then refined one dimension at a time: inside
+// aligned groups of consecutive positions the extents are re-sorted by their
+// lower bound in the next dimension (k_rekey builds (group, key(lo_k))
+// keys).  Each group stays a contiguous range of the dimension-0 order, so
+// the top of the tree still follows the paper's lower-bound order, while the
+// small subtrees near the leaves become compact in every dimension.
+#include "ddm_internal.cuh"
+
+namespace ddm {
+namespace {
+
+constexpr int kThreads = 256;
+
+__global__ void __launch_bounds__(kThreads)
+k_validate(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
+           unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals, int key_mode,
+           Status* __restrict__ st) {
+  bool bad = false;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+    // Row loads are coalesced: consecutive lanes read consecutive floats.
+    for (int k = 0; k < d; ++k) {
+      const float a = __ldg(lo + (size_t)k * cnt + i);
+      const float b = __ldg(hi + (size_t)k * cnt + i);
+      bad |= !(a <= b);  // false for NaN as well as for lo > hi
+    }
+    if (keys) {
+      const float a = __ldg(lo + i), b = __ldg(hi + i);
+      keys[i] = key_mode == 1 ? ((unsigned long long)float_key(a) << 32) | float_key(b)
+                              : (unsigned long long)float_key(a);
+      vals[i] = i;
+    }
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->err, kErrExtent);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rekey(const uint32_t* __restrict__ vals, const float* __restrict__ lo_k, uint32_t cnt, int glog2,
+        unsigned long long* __restrict__ keys) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride)
+    keys[i] = ((unsigned long long)(i >> glog2) << 32) | float_key(__ldg(lo_k + vals[i]));
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_gather(int d, const uint32_t* __restrict__ vals, const float* __restrict__ lo,
+         const float* __restrict__ hi, uint32_t cnt, float2* __restrict__ qe,
+         uint32_t* __restrict__ qid) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+    const uint32_t id = vals[i];
+    qid[i] = id;
+    for (int k = 0; k < d; ++k)
+      qe[(size_t)k * cnt + i] = make_float2(__ldg(lo + (size_t)k * cnt + id),
+                                            __ldg(hi + (size_t)k * cnt + id));
+  }
+}
+
+uint32_t grid_for(uint32_t cnt, int sms) {
+  uint32_t blocks = (cnt + kThreads - 1) / kThreads;
+  const uint32_t cap = (uint32_t)sms * 8u;
+  return blocks > cap ? cap : (blocks ? blocks : 1);
+}
+
+}  // namespace
+
+cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, int glog2,
+                         unsigned long long* keys, int sms, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  k_rekey<<<grid_for(cnt, sms), kThreads, 0, s>>>(vals, lo_k, cnt, glog2, keys);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const float* hi,
+                          uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  k_gather<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, vals, lo, hi, cnt, qe, qid);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate(int d, const float* lo, const float* hi, uint32_t cnt,
+                            unsigned long long* keys, uint32_t* vals, int key_mode, Status* st,
+                            int sms, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  k_validate<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, keys, vals, key_mode, st);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

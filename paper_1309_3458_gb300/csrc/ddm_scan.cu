@@ -1,0 +1,181 @@
+// Exclusive scan of the per-update match counts into 64-bit offsets.
+//
+// The intersection matrix M of Section III is sparse and is returned in
+// compressed form: update j's matches occupy [offsets[j], offsets[j+1]) of
+// the pair list, and offsets[m] = K (which can exceed 2^32).  Classic
+// reduce-then-scan over tiles of 4096 counts: per-tile sums, one CTA scans
+// the tile sums, then each tile scans its counts from its tile offset.  No
+// kernel waits on another CTA.
+#include "ddm_internal.cuh"
+
+namespace ddm {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = kScanTile / kThreads;  // 16
+
+__device__ __forceinline__ unsigned long long warp_incl_scan(unsigned long long x, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  return x;
+}
+
+// Exclusive block-wide scan of one value per thread; returns the thread's
+// exclusive prefix and the block total in *total.
+__device__ unsigned long long block_excl_scan(unsigned long long v, unsigned long long* total) {
+  __shared__ unsigned long long wsum[kThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const unsigned long long incl = warp_incl_scan(v, lane);
+  if (lane == 31) wsum[w] = incl;
+  __syncthreads();
+  unsigned long long pre = 0, tot = 0;
+#pragma unroll
+  for (int i = 0; i < kThreads / 32; ++i) {
+    if (i < w) pre += wsum[i];
+    tot += wsum[i];
+  }
+  __syncthreads();
+  *total = tot;
+  return pre + incl - v;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_tile_sums(const uint32_t* __restrict__ counts, uint32_t m, unsigned long long* __restrict__ sums) {
+  const size_t base = (size_t)blockIdx.x * kScanTile;
+  unsigned long long s = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const size_t idx = base + (size_t)i * kThreads + threadIdx.x;  // coalesced
+    if (idx < m) s += counts[idx];
+  }
+  unsigned long long tot;
+  block_excl_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// One CTA: exclusive scan of the tile sums in place; total -> offsets[m], st->K.
+__global__ void __launch_bounds__(kThreads)
+k_scan_sums(unsigned long long* __restrict__ sums, uint32_t tiles, unsigned long long* __restrict__ offsets,
+            uint32_t m, Status* __restrict__ st) {
+  unsigned long long carry = 0;
+  for (uint32_t c = 0; c < tiles; c += kThreads) {
+    const uint32_t idx = c + threadIdx.x;
+    const unsigned long long v = idx < tiles ? sums[idx] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan(v, &tot);
+    if (idx < tiles) sums[idx] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) {
+    offsets[m] = carry;
+    if (st) st->K = carry;
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned long long* __restrict__ sums,
+             unsigned long long* __restrict__ offsets) {
+  __shared__ uint32_t s_c[kScanTile];
+  const size_t base = (size_t)blockIdx.x * kScanTile;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const size_t idx = base + (size_t)i * kThreads + threadIdx.x;
+    s_c[i * kThreads + threadIdx.x] = idx < m ? counts[idx] : 0u;
+  }
+  __syncthreads();
+  // thread t scans items [t*16, t*16+16) of the tile
+  unsigned long long local = 0;
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) local += s_c[threadIdx.x * kItems + i];
+  unsigned long long tot;
+  unsigned long long run = sums[blockIdx.x] + block_excl_scan(local, &tot);
+  unsigned long long out[kItems];
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    out[i] = run;
+    run += s_c[threadIdx.x * kItems + i];
+  }
+  // write back: reuse shared memory as 64-bit staging in two halves
+  __syncthreads();
+  unsigned long long* s_o = reinterpret_cast<unsigned long long*>(s_c);  // 2048 entries
+#pragma unroll
+  for (int half = 0; half < 2; ++half) {
+    const int lo_t = half * (kThreads / 2);
+    if ((int)threadIdx.x >= lo_t && (int)threadIdx.x < lo_t + kThreads / 2) {
+#pragma unroll
+      for (int i = 0; i < kItems; ++i) s_o[(threadIdx.x - lo_t) * kItems + i] = out[i];
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < kScanTile / 2; q += kThreads) {
+      const size_t idx = base + (size_t)half * (kScanTile / 2) + q;
+      if (idx < m) offsets[idx] = s_o[q];
+    }
+    __syncthreads();
+  }
+}
+
+// Largest e in [begin, m] with offsets[e] - offsets[begin] <= capacity.
+__global__ void k_chunk_end(const unsigned long long* __restrict__ offsets, uint32_t m, uint32_t begin,
+                            unsigned long long capacity, Status* __restrict__ st) {
+  const unsigned long long b0 = offsets[begin];
+  uint32_t lo = begin, hi = m;  // invariant: offsets[lo] - b0 <= capacity
+  while (lo < hi) {
+    const uint32_t mid = lo + (hi - lo + 1) / 2;
+    if (offsets[mid] - b0 <= capacity) lo = mid; else hi = mid - 1;
+  }
+  st->aux = lo;
+  st->K = offsets[lo] - b0;
+}
+
+__global__ void k_flags(const uint32_t* __restrict__ qid, uint32_t m, uint32_t begin, uint32_t end,
+                        uint32_t* __restrict__ flags) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x) {
+    const uint32_t v = qid[i];
+    flags[i] = (v >= begin && v < end) ? 1u : 0u;
+  }
+}
+
+__global__ void k_compact(const uint32_t* __restrict__ flags, const unsigned long long* __restrict__ offs,
+                          uint32_t m, uint32_t* __restrict__ list) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < m; i += gridDim.x * blockDim.x)
+    if (flags[i]) list[offs[i]] = i;
+}
+
+}  // namespace
+
+cudaError_t launch_select(const uint32_t* qid, uint32_t m, uint32_t begin, uint32_t end,
+                          uint32_t* flags, unsigned long long* offs, unsigned long long* sums,
+                          uint32_t* list, Status* st, cudaStream_t s) {
+  (void)st;
+  if (m == 0) return cudaSuccess;
+  uint32_t blocks = (m + 255) / 256;
+  if (blocks > 2048) blocks = 2048;
+  k_flags<<<blocks, 256, 0, s>>>(qid, m, begin, end, flags);
+  cudaError_t e = launch_scan(flags, m, offs, sums, nullptr, s);
+  if (e) return e;
+  k_compact<<<blocks, 256, 0, s>>>(flags, offs, m, list);
+  note_launches(2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const uint32_t* counts, uint32_t m, unsigned long long* offsets,
+                        unsigned long long* block_sums, Status* st, cudaStream_t s) {
+  const uint32_t tiles = (m + kScanTile - 1) / kScanTile;
+  if (tiles > 0) k_tile_sums<<<tiles, kThreads, 0, s>>>(counts, m, block_sums);
+  k_scan_sums<<<1, kThreads, 0, s>>>(block_sums, tiles, offsets, m, st);
+  if (tiles > 0) k_scan_tiles<<<tiles, kThreads, 0, s>>>(counts, m, block_sums, offsets);
+  note_launches(tiles > 0 ? 3u : 1u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chunk_end(const unsigned long long* offsets, uint32_t m, uint32_t begin,
+                             unsigned long long capacity, Status* st, cudaStream_t s) {
+  k_chunk_end<<<1, 1, 0, s>>>(offsets, m, begin, capacity, st);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

@@ -1,0 +1,169 @@
+// Implicit interval tree build (Section IV, Interval-Tree-Create of Alg. 5).
+//
+// The paper stores the subscriptions in an augmented AVL tree ordered by
+// lower bound, each node keeping maxupper and minlower of its subtree, and
+// notes that any interval tree may stand in for it.  The GPU keeps the order
+// and the two subtree bounds in a flattened, pointer-free form:
+//
+//   * the sorted subscriptions themselves are the leaves;
+//   * a level-l node g covers the sorted positions [g*32^l, (g+1)*32^l) and
+//     stores (minlower, maxupper) of that range -- for every dimension, so
+//     that the d-dimensional test of Section III-A prunes whole subtrees;
+//   * the top level has at most 32 nodes, so one warp tests it in one step.
+//
+// The bounds are min/max reductions done with warp shuffles (32 children
+// per warp), level by level from the leaves up.  The element order comes
+// from ddm_layout.cu / ddm_sort.cu: dimension-0 (lower, upper, id), refined
+// inside aligned groups by the lower bound of the other dimensions.
+#include <cfloat>
+#include <cmath>
+
+#include "ddm_internal.cuh"
+
+namespace ddm {
+namespace {
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ float warp_min(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Gather the sorted SoA layout and build levels 1 and 2.  One CTA of 1024
+// threads covers 1024 sorted positions: one warp per level-1 node, and the
+// CTA's 32 level-1 nodes form level-2 node blockIdx.x.
+__global__ void __launch_bounds__(1024)
+k_gather_build(TreeView t, const uint32_t* __restrict__ sorted_ids, const float* __restrict__ lo,
+               const float* __restrict__ hi, float2* __restrict__ e, uint32_t* __restrict__ sid,
+               float2* __restrict__ nodes) {
+  __shared__ float s_min[DDM_MAX_DIMS][32], s_max[DDM_MAX_DIMS][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t n = t.n;
+  const uint32_t i = blockIdx.x * 1024u + threadIdx.x;
+  const bool valid = i < n;
+  uint32_t id = 0;
+  if (valid) {
+    id = sorted_ids[i];
+    sid[i] = id;
+  }
+  const uint32_t g = blockIdx.x * 32u + w;
+  const bool gvalid = g < t.cnt[1];
+  for (int k = 0; k < t.d; ++k) {
+    float a = FLT_MAX, b = -FLT_MAX;
+    if (valid) {
+      a = lo[(size_t)k * n + id];
+      b = hi[(size_t)k * n + id];
+      e[(size_t)k * n + i] = make_float2(a, b);
+    }
+    const float mn = warp_min(valid ? a : INFINITY);
+    const float mx = warp_max(valid ? b : -INFINITY);
+    if (lane == 0) {
+      if (gvalid) nodes[(size_t)k * t.total + t.off[1] + g] = make_float2(mn, mx);
+      s_min[k][w] = gvalid ? mn : INFINITY;
+      s_max[k][w] = gvalid ? mx : -INFINITY;
+    }
+  }
+  if (t.L < 2) return;
+  __syncthreads();
+  if (w < t.d) {
+    const float mn = warp_min(s_min[w][lane]);
+    const float mx = warp_max(s_max[w][lane]);
+    if (lane == 0) nodes[(size_t)w * t.total + t.off[2] + blockIdx.x] = make_float2(mn, mx);
+  }
+}
+
+// Levels 3..L (at most n / 32768 nodes): one CTA walks up level by level.
+__global__ void __launch_bounds__(1024) k_build_upper(TreeView t, float2* __restrict__ nodes) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int l = 3; l <= t.L; ++l) {
+    const uint32_t child_cnt = t.cnt[l - 1];
+    for (uint32_t g = w; g < t.cnt[l]; g += 32) {
+      const uint32_t c = g * 32u + lane;
+      for (int k = 0; k < t.d; ++k) {
+        const float2* child = nodes + (size_t)k * t.total + t.off[l - 1];
+        const float2 v = c < child_cnt ? child[c] : make_float2(INFINITY, -INFINITY);
+        const float mn = warp_min(v.x);
+        const float mx = warp_max(v.y);
+        if (lane == 0) nodes[(size_t)k * t.total + t.off[l] + g] = make_float2(mn, mx);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_export_nodes(const float2* __restrict__ nodes, size_t total,
+                               float* __restrict__ node_lo, float* __restrict__ node_hi) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const float2 v = nodes[i];
+    if (node_lo) node_lo[i] = v.x;
+    if (node_hi) node_hi[i] = v.y;
+  }
+}
+
+}  // namespace
+
+void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* total) {
+  for (int l = 0; l <= kMaxLevels; ++l) cnt[l] = off[l] = 0;
+  int lv = 1;
+  cnt[1] = (n + kFan - 1) / kFan;
+  while (cnt[lv] > (uint32_t)kFan) {
+    cnt[lv + 1] = (cnt[lv] + kFan - 1) / kFan;
+    ++lv;
+  }
+  uint32_t acc = 0;
+  for (int l = 1; l <= lv; ++l) {
+    off[l] = acc;
+    acc += cnt[l];
+  }
+  *L = lv;
+  *total = acc;
+}
+
+// Sort-tile-recursive split: with nb = n/32 leaves, each dimension gets about
+// nb^(1/d) slabs; dimension k >= 1 is re-sorted inside groups of
+// 32 * nb^((d-k)/d) positions, rounded to a power of two.  glog2[k] = 0 means
+// no re-sort (groups would not be smaller than the previous ones or would
+// hold a single leaf).
+void str_groups(uint32_t n, int d, int* glog2) {
+  for (int k = 0; k < DDM_MAX_DIMS; ++k) glog2[k] = 0;
+  const double nb = std::ceil((double)n / kFan);
+  int prev = 64;
+  for (int k = 1; k < d; ++k) {
+    const double G = kFan * std::pow(nb, (double)(d - k) / d);
+    const int g = (int)std::floor(std::log2(G) + 0.5);
+    if (g >= 6 && g < prev && ((uint64_t)1 << g) < n) {
+      glog2[k] = g;
+      prev = g;
+    }
+  }
+}
+
+cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
+                         const float* hi, float2* e, uint32_t* sid, float2* nodes,
+                         cudaStream_t s) {
+  if (t.n == 0) return cudaSuccess;
+  const uint32_t blocks = (t.n + 1023) / 1024;
+  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, e, sid, nodes);
+  if (t.L >= 3) k_build_upper<<<1, 1024, 0, s>>>(t, nodes);
+  note_launches(t.L >= 3 ? 2u : 1u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s) {
+  const size_t total = (size_t)t.total * t.d;
+  if (total == 0 || (!node_lo && !node_hi)) return cudaSuccess;
+  const size_t blocks = (total + 255) / 256;
+  k_export_nodes<<<blocks < 1024 ? (unsigned)blocks : 1024u, 256, 0, s>>>(t.nodes, total, node_lo,
+                                                                       node_hi);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+}  // namespace ddm

@@ -1,0 +1,78 @@
+"""The C-ABI library loads and exports every entry point of include/ddm.h.
+
+Host-only checks: no call here launches GPU work.  Argument errors are
+detected before any CUDA call, so they are checked on the CPU as well.
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1309_3458_gb300 as ddm
+from paper_1309_3458_gb300 import build as B
+
+HEADER = os.path.join(B.INCLUDE, "ddm.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return ddm.lib()
+
+
+def declared():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ddm_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_header_declarations_match_binding():
+    assert declared() == sorted(ddm.SIGNATURES)
+
+
+def test_every_symbol_exported(lib):
+    for name in declared():
+        assert hasattr(lib, name), name
+
+
+def test_strerror(lib):
+    for code in range(8):
+        assert ddm.ddm_strerror(code)
+    assert ddm.ddm_strerror(99) == "unknown error"
+
+
+def test_argument_errors_without_gpu(lib):
+    k = ctypes.c_uint64(0)
+    assert lib.ddm_create(None, 0) == ddm.DDM_ERR_ARG
+    assert lib.ddm_destroy(None) == ddm.DDM_OK
+    assert lib.ddm_count(None, 1, None, None, 0, None, None, 0, 0, ctypes.byref(k), None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_match(None, 1, None, None, 0, None, None, 0, 0, None, 0, ctypes.byref(k), None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_build(None, 1, None, None, 0, None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_plan(None, None, None, 0, 0, None, None, None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_write(None, 0, 0, None, 0, None, None) == ddm.DDM_ERR_ARG
+    e = ctypes.c_uint32(0)
+    assert lib.ddm_chunk_end(None, 0, 0, ctypes.byref(e), None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_tree_shape(None, None, None, None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_tree_export(None, None, None, None, None) == ddm.DDM_ERR_ARG
+    assert lib.ddm_debug_set_alloc_limit(None, 0) == ddm.DDM_ERR_ARG
+
+
+def test_create_reports_missing_device(lib):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    h = ctypes.c_void_p()
+    assert lib.ddm_create(ctypes.byref(h), 0) == ddm.DDM_ERR_CUDA
+    assert h.value is None
+
+
+def test_product_path_does_not_import_oracle():
+    # The binding, the kernels and the build script never load the oracle.
+    pkg = os.path.dirname(ddm.__file__)
+    pat = re.compile(r"^\s*(import\s+oracle|from\s+oracle\b)|libddm_oracle|ddm_oracle\.c|oracle_[a-z]+\(",
+                     re.M)
+    for root, _, files in os.walk(pkg):
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h")):
+                assert not pat.search(open(os.path.join(root, f)).read()), f

@@ -1,0 +1,276 @@
+"""GPU parity: libddm (through its C ABI) against the CPU oracle.
+
+Integer results (pair sets, per-update counts, the sorted order) must be
+bit-exact.  The method only compares float32 coordinates, so there is no
+floating-point tolerance: both sides compare the same bytes.
+
+Both sides group pairs by update id, so the update column is compared
+element by element.  Within one update the library reports pairs in the
+order of its tree's leaves.  For d = 1 that order is dimension-0 (lower,
+upper, id), the order of the oracle's in-order interval tree walk, and the
+whole list is compared element by element.  For d > 1 the GPU tree refines
+the order near the leaves, so the subscription column is compared as a set
+per update, and the order is checked against the tree's exported order.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1309_3458_gb300 as ddm
+from paper_1309_3458_gb300 import workloads as W
+from tests.helpers import gpu_match, gpu_offsets, keys, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import __graft_entry__
+    __graft_entry__.build()
+    h = ddm.ddm_create(0)
+    yield h
+    ddm.ddm_destroy(h)
+
+
+def tree_rank(ctx, n):
+    """rank[sub id] = position of the subscription in the built tree."""
+    import torch
+    order = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+    ddm.ddm_tree_export(ctx, order)
+    torch.cuda.synchronize()
+    order = order[:n].cpu().numpy().view(np.uint32)
+    assert np.array_equal(np.sort(order), np.arange(n, dtype=np.uint32))
+    rank = np.empty(n, np.int64)
+    rank[order] = np.arange(n)
+    return rank
+
+
+def check_exact(ctx, arrays, flags=0):
+    d, n = arrays[2].shape
+    K, pu, ps = gpu_match(ctx, arrays, flags)
+    Ko, ou, os_ = oracle.itm_pairs(*arrays, flags=flags)
+    assert K == Ko
+    assert np.array_equal(pu, ou)
+    if d == 1:
+        assert np.array_equal(ps, os_)
+    else:
+        assert np.array_equal(keys(pu, ps) if K == 0 else np.sort(keys(pu, ps)),
+                              np.sort(keys(ou, os_)))
+    if K:
+        # within an update, pairs follow the tree's order; no duplicates
+        r = tree_rank(ctx, n)[ps]
+        same = pu[1:] == pu[:-1]
+        assert (r[1:][same] > r[:-1][same]).all()
+    return K
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_tiny_grids_with_ties(ctx, d, flags):
+    for seed in range(10):
+        rng = np.random.default_rng(1000 + seed)
+        n, m = (int(v) for v in rng.integers(1, 300, size=2))
+        arrays = W.grid_random(n, m, d, seed=seed, grid=6)
+        check_exact(ctx, arrays, flags)
+        K_bf = oracle.bf(*arrays, flags=flags, pairs=False)[0]
+        assert K_bf == gpu_match(ctx, arrays, flags)[0]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("k", [1, 2, 7, 40])
+def test_lattice_closed_forms(ctx, d, k):
+    if k ** d > 70000:
+        k = int(round(70000 ** (1 / d)))
+    for shift, want_c, want_o in ((False, (3 * k - 2) ** d, k ** d),
+                                  (True, (2 * k - 1) ** d, (2 * k - 1) ** d)):
+        arrays = W.lattice(k, d, shift_half=shift)
+        assert gpu_match(ctx, arrays, 0)[0] == want_c
+        assert gpu_match(ctx, arrays, 1)[0] == want_o
+
+
+def test_fig1_worked_example(ctx):
+    from tests.test_oracle import load_fig1
+    arrays, M, _ = load_fig1()
+    for flags in (0, 1):
+        K, pu, ps = gpu_match(ctx, arrays, flags)
+        got = np.zeros(M.shape, int)
+        got[ps, pu] = 1
+        assert np.array_equal(got, M)
+
+
+@pytest.mark.parametrize("n,m", [(1, 1), (31, 7), (32, 32), (33, 1), (1023, 999), (1025, 2048),
+                                 (4095, 4097), (32769, 5000), (40000, 33)])
+def test_ragged_sizes(ctx, n, m):
+    arrays = W.uniform_fixed_length(n, m, 2, min(300.0, 0.25 * (n + m)), seed=n + m)
+    check_exact(ctx, arrays)
+
+
+def test_empty_sets(ctx):
+    import torch
+    for n, m in ((0, 10), (10, 0), (0, 0)):
+        arrays = W.uniform_fixed_length(max(n, 1), max(m, 1), 2, 1.0, seed=1)
+        arrays = (arrays[0][:, :m].copy(), arrays[1][:, :m].copy(),
+                  arrays[2][:, :n].copy(), arrays[3][:, :n].copy())
+        U = to_dev(arrays)
+        assert ddm.ddm_count(ctx, *U) == 0
+        pairs = torch.empty((4, 2), dtype=torch.int32, device="cuda")
+        assert ddm.ddm_match(ctx, *U, pairs) == 0
+
+
+def test_special_values(ctx):
+    # -0.0 against +0.0, infinite bounds, identical extents, degenerate points
+    lo = np.array([[-0.0, 0.0, -np.inf, 5.0, 5.0, 5.0, 1e30, -1e-30]], np.float32)
+    hi = np.array([[0.0, 0.0, np.inf, 5.0, 5.0, 6.0, np.inf, 0.0]], np.float32)
+    arrays = (lo.copy(), hi.copy(), lo.copy(), hi.copy())
+    for flags in (0, 1):
+        check_exact(ctx, arrays, flags)
+
+
+def test_all_identical_extents(ctx):
+    lo = np.full((2, 3000), 7.0, np.float32)
+    hi = np.full((2, 3000), 9.0, np.float32)
+    K = check_exact(ctx, (lo[:, :1000].copy(), hi[:, :1000].copy(), lo, hi))
+    assert K == 1000 * 3000
+
+
+def test_tree_order_and_node_bounds(ctx):
+    import torch
+    arrays = W.clustered_lognormal(70000, 10, d=3, alpha=100.0, seed=4)
+    U = to_dev(arrays)
+    ddm.ddm_build(ctx, U[2], U[3])
+    L, counts, total = ddm.ddm_tree_shape(ctx)
+    n = arrays[2].shape[1]
+    order = torch.empty(n, dtype=torch.int32, device="cuda")
+    nlo = torch.empty(3 * total, dtype=torch.float32, device="cuda")
+    nhi = torch.empty(3 * total, dtype=torch.float32, device="cuda")
+    ddm.ddm_tree_export(ctx, order, nlo, nhi)
+    torch.cuda.synchronize()
+    order = order.cpu().numpy().view(np.uint32)
+    assert np.array_equal(np.sort(order), np.arange(n, dtype=np.uint32))
+    # node bounds: per dimension, min lower / max upper over each node's range
+    nlo = nlo.cpu().numpy().reshape(3, total)
+    nhi = nhi.cpu().numpy().reshape(3, total)
+    assert counts[-1] <= 32 and sum(counts) == total
+    for k in range(3):
+        lo, hi = arrays[2][k][order], arrays[3][k][order]
+        pos = 0
+        for lvl, c in enumerate(counts, start=1):
+            span = 32 ** lvl
+            pad = c * span - n
+            mn = np.concatenate([lo, np.full(pad, np.inf, np.float32)]).reshape(c, span).min(1)
+            mx = np.concatenate([hi, np.full(pad, -np.inf, np.float32)]).reshape(c, span).max(1)
+            assert np.array_equal(nlo[k, pos:pos + c], mn) and np.array_equal(nhi[k, pos:pos + c], mx)
+            pos += c
+    # Re-sort groups are aligned powers of two smaller than n, so every
+    # aligned block of 2^16 positions holds exactly the extents that the
+    # paper's dimension-0 (lower, upper, id) order puts there.
+    want, _ = oracle.tree_order(arrays[2][0], arrays[3][0])
+    blk = 1 << 16
+    for b in range(0, n, blk):
+        assert np.array_equal(np.sort(order[b:b + blk]), np.sort(want[b:b + blk]))
+
+
+def test_tree_order_d1_is_paper_order(ctx):
+    import torch
+    arrays = W.grid_random(50000, 10, 1, seed=8, grid=300)
+    U = to_dev(arrays)
+    ddm.ddm_build(ctx, U[2], U[3])
+    order = torch.empty(50000, dtype=torch.int32, device="cuda")
+    ddm.ddm_tree_export(ctx, order)
+    torch.cuda.synchronize()
+    want, _ = oracle.tree_order(arrays[2][0], arrays[3][0])
+    assert np.array_equal(order.cpu().numpy().view(np.uint32), want)
+
+
+@pytest.mark.parametrize("name,scale", [("uniform_d1_N1e4_a1", 1.0),
+                                        ("uniform_d1_N1e6_a0.01", 0.01),
+                                        ("uniform_d1_N1e6_a1", 0.01),
+                                        ("uniform_d1_N1e6_a100", 0.01),
+                                        ("uniform_d2_N1e6_a0.01", 0.01),
+                                        ("uniform_d2_N1e6_a1", 0.01),
+                                        ("uniform_d2_N1e6_a100", 0.01),
+                                        ("clustered_d3_N1e7_a100", 0.001)])
+def test_scaled_configs_exact(ctx, name, scale):
+    arrays = W.make(name, scale)
+    for flags in (0, 1):
+        check_exact(ctx, arrays, flags)
+
+
+def test_staged_chunks_reproduce_full_output(ctx):
+    import torch
+    arrays = W.uniform_fixed_length(20000, 30000, 2, 100.0, seed=9)
+    K, pu, ps = gpu_match(ctx, arrays)
+    U = to_dev(arrays)
+    ddm.ddm_build(ctx, U[2], U[3])
+    off = torch.empty(30001, dtype=torch.int64, device="cuda")
+    assert ddm.ddm_plan(ctx, U[0], U[1], offsets=off) == K
+    off = off.cpu().numpy()
+    cap = K // 7 + 1
+    buf = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+    got, b = [], 0
+    while b < 30000:
+        e = ddm.ddm_chunk_end(ctx, b, cap)
+        assert e > b and off[e] - off[b] <= cap and (e == 30000 or off[e + 1] - off[b] > cap)
+        k = ddm.ddm_write(ctx, b, e, buf)
+        assert k == off[e] - off[b]
+        got.append(buf[:k].cpu().numpy().view(np.uint32).copy())
+        b = e
+    got = np.concatenate(got)
+    assert np.array_equal(got[:, 0], pu) and np.array_equal(got[:, 1], ps)
+    # match_range gives the same slice
+    buf2 = torch.empty((K, 2), dtype=torch.int32, device="cuda")
+    k = ddm.ddm_match_range(ctx, *U, 1234, 4321, buf2)
+    sl = buf2[:k].cpu().numpy().view(np.uint32)
+    assert np.array_equal(sl[:, 0], pu[off[1234]:off[4321]])
+    assert np.array_equal(sl[:, 1], ps[off[1234]:off[4321]])
+
+
+# --- error paths -------------------------------------------------------------
+
+def test_invalid_extents(ctx):
+    base = W.uniform_fixed_length(500, 400, 2, 10.0, seed=2)
+    for which, idx, val in ((0, (1, 17), np.nan), (1, (0, 3), -1.0), (2, (1, 499), np.nan),
+                            (3, (0, 0), -5.0)):
+        arrays = [a.copy() for a in base]
+        arrays[which][idx] = val
+        U = to_dev(arrays)
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_count(ctx, *U)
+        assert e.value.code == ddm.DDM_ERR_EXTENT
+    # the context stays usable
+    check_exact(ctx, base)
+
+
+def test_capacity_and_state_errors(ctx):
+    import torch
+    arrays = W.uniform_fixed_length(3000, 3000, 1, 50.0, seed=3)
+    U = to_dev(arrays)
+    K = ddm.ddm_count(ctx, *U)
+    small = torch.full((K - 1, 2), -1, dtype=torch.int32, device="cuda")
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.ddm_match(ctx, *U, small)
+    assert e.value.code == ddm.DDM_ERR_CAPACITY and e.value.k == K
+    assert (small == -1).all()          # nothing written when it does not fit
+    fresh = ddm.ddm_create(0)
+    try:
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_plan(fresh, U[0], U[1])
+        assert e.value.code == ddm.DDM_ERR_STATE
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_write(fresh, 0, 1, small)
+        assert e.value.code == ddm.DDM_ERR_STATE
+        ddm.ddm_debug_set_alloc_limit(fresh, 1 << 16)
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_count(fresh, *U)
+        assert e.value.code == ddm.DDM_ERR_NOMEM
+        ddm.ddm_debug_set_alloc_limit(fresh, 0)
+        assert ddm.ddm_count(fresh, *U) == K
+    finally:
+        ddm.ddm_destroy(fresh)
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.ddm_match_range(ctx, *U, 10, 5, small)
+    assert e.value.code == ddm.DDM_ERR_ARG
+    bad = to_dev([np.zeros((9, 4), np.float32)] * 4)
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.ddm_count(ctx, *bad)
+    assert e.value.code == ddm.DDM_ERR_ARG
