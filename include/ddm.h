@@ -193,6 +193,33 @@ int ddm_tree_export(ddm_ctx *ctx, uint32_t *order, float *node_lo, float *node_h
  * context's total above `bytes` fail with DDM_ERR_NOMEM (0 = no limit). */
 int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);
 
+/* ---------------------------------------------------------------------- */
+/* Allocation-free offsets scan                                            */
+/* ---------------------------------------------------------------------- */
+
+/* The paper has no counterpart to this call; it serves callers that cannot
+ * allocate device memory when they need it: code recording a stream into a
+ * CUDA graph (cudaMalloc cannot be captured), real-time loops that must not
+ * block in the allocator, hosts whose device memory all belongs to another
+ * allocator.
+ *
+ * Exclusive prefix sum of per-update match counts: offsets[j] =
+ * counts[0] + ... + counts[j-1] for j <= m, so update j's pairs are
+ * [offsets[j], offsets[j+1]) of a pair list grouped by update and
+ * offsets[m] = K -- the same result as the offsets of ddm_plan for the same
+ * counts.  counts (m uint32) and offsets (m + 1 uint64) are DEVICE pointers
+ * of the current device, owned by the caller; work is enqueued on `stream`
+ * and nothing is synchronised or allocated.  Scratch is a fixed device
+ * array inside the library, so m must not exceed DDM_NOALLOC_MAX_UPDATES
+ * (DDM_ERR_ARG otherwise; also for NULL pointers).  The array is shared by
+ * every call on a device: calls whose work may overlap on the GPU race and
+ * must be serialised by the caller.  The first call on a device looks up
+ * the array's device address (DDM_ERR_CUDA if that fails); make that first
+ * call before any stream capture. */
+#define DDM_NOALLOC_MAX_UPDATES 67108864u  /* 2^26 updates: 128 KiB of scratch */
+int ddm_scan_counts_noalloc(const uint32_t *counts, uint32_t m, uint64_t *offsets,
+                            void *stream);
+
 /* Number of CUDA kernels this library has launched in the calling process
  * since it was loaded (all contexts).  Host-side counter, no GPU access. */
 uint64_t ddm_debug_launch_count(void);

@@ -35,6 +35,7 @@ DDM_OPEN = 1
 DDM_MAX_DIMS = 8
 DDM_MAX_EXTENTS = (1 << 30) - 1
 DDM_MAX_TREE_LEVELS = 8
+DDM_NOALLOC_MAX_UPDATES = 1 << 26
 
 # Every entry point declared in include/ddm.h, with its ctypes signature.
 _vp, _i, _u32, _u64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_uint32, ctypes.c_uint64
@@ -56,6 +57,7 @@ SIGNATURES = {
     "ddm_tree_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ddm_debug_set_alloc_limit": (_i, [_vp, _u64]),
     "ddm_debug_launch_count": (_u64, []),
+    "ddm_scan_counts_noalloc": (_i, [_vp, _u32, _vp, _vp]),
 }
 
 _lib = None
@@ -215,3 +217,10 @@ def ddm_debug_set_alloc_limit(ctx: int, nbytes: int) -> None:
 
 def ddm_debug_launch_count() -> int:
     return int(lib().ddm_debug_launch_count())
+
+
+def ddm_scan_counts_noalloc(counts, offsets, stream=None) -> None:
+    """Offsets (int64 device tensor, m + 1) from per-update counts (int32
+    device tensor, m) without any allocation; see include/ddm.h."""
+    _check(lib().ddm_scan_counts_noalloc(_ptr(counts), counts.shape[0], _ptr(offsets),
+                                         _stream(stream)), "ddm_scan_counts_noalloc")

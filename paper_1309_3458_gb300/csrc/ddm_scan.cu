@@ -178,4 +178,67 @@ cudaError_t launch_chunk_end(const unsigned long long* offsets, uint32_t m, uint
   return cudaGetLastError();
 }
 
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the offsets scan (ddm_scan_counts_noalloc).
+//
+// Some callers cannot allocate device memory at the moment they need the
+// offsets: a stream being captured into a CUDA graph (cudaMalloc cannot be
+// captured), a real-time loop that must not block in the allocator, or a
+// host that hands all device memory to its own pool.  This entry point runs
+// the same three scan kernels as launch_scan, with the per-tile sums kept in
+// a fixed device array instead of a context buffer.
+//
+// Limits and sharing: the array holds kNoallocTiles tile sums, so m may be
+// at most DDM_NOALLOC_MAX_UPDATES (= kNoallocTiles * 4096); every GPU that
+// loads the library holds the array (128 KiB) until the process exits.  All
+// calls share it, so calls whose kernels overlap on the GPU (different
+// streams, or different host threads) race and must be serialised by the
+// caller.  Each call writes every tile sum it later reads, so nothing
+// needs clearing between calls.
+// ---------------------------------------------------------------------------
+constexpr uint32_t kNoallocTiles = DDM_NOALLOC_MAX_UPDATES / kScanTile;
+static_assert(DDM_NOALLOC_MAX_UPDATES % kScanTile == 0, "limit must be whole tiles");
+
+static __device__ __align__(256) unsigned long long g_noalloc_tile_sums[kNoallocTiles];
+
+namespace {
+
+// Device address of g_noalloc_tile_sums per device, looked up once per device
+// (host code cannot use the symbol itself as a device pointer).
+constexpr int kMaxDevices = 64;
+unsigned long long* g_noalloc_ptr[kMaxDevices] = {};
+
+}  // namespace
+
 }  // namespace ddm
+
+extern "C" int ddm_scan_counts_noalloc(const uint32_t* counts, uint32_t m, uint64_t* offsets,
+                                       void* stream) {
+  using namespace ddm;
+  if (!offsets || (m > 0 && !counts)) return DDM_ERR_ARG;
+  if (m > DDM_NOALLOC_MAX_UPDATES) return DDM_ERR_ARG;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return DDM_ERR_CUDA;
+  }
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_tile_sums) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return DDM_ERR_CUDA;
+    }
+    g_noalloc_ptr[dev] = static_cast<unsigned long long*>(p);
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const uint32_t tiles = (m + kScanTile - 1) / kScanTile;
+  unsigned long long* sums = g_noalloc_ptr[dev];
+  auto* off = reinterpret_cast<unsigned long long*>(offsets);
+  if (tiles > 0) k_tile_sums<<<tiles, kThreads, 0, s>>>(counts, m, sums);
+  k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, off, m, nullptr);
+  if (tiles > 0) k_scan_tiles<<<tiles, kThreads, 0, s>>>(counts, m, sums, off);
+  note_launches(tiles > 0 ? 3u : 1u);
+  if (cudaGetLastError() != cudaSuccess) return DDM_ERR_CUDA;
+  return DDM_OK;
+}
