@@ -3,8 +3,9 @@
 
 A step is one whole match of the workload: sort and tree build over the
 subscriptions (ddm_build), the counting pass and scan over all updates
-(ddm_plan), then the write pass in update ranges whose pairs fit the device
-pair buffer (ddm_chunk_end + ddm_write), every pair written to HBM.  Inputs
+(ddm_plan), then the write pass over ranges of the plan order whose pairs fit
+the device pair buffer (ddm_chunk_end_ordered + ddm_write_ordered), every pair
+written to HBM.  Inputs
 (240 MB for the default workload) are larger than L2, so no flush is needed.
 
 Default workload: d = 3, 5e6 updates + 5e6 subscriptions, centres from 64
@@ -221,11 +222,11 @@ def main():
         K = ddm.ddm_plan(ctx, dev[0], dev[1])
         b = 0
         while b < m:
-            e = ddm.ddm_chunk_end(ctx, b, cap)
+            e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
             if record:
                 s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 s0.record(stream)
-            k = ddm.ddm_write(ctx, b, e, pairs)
+            k = ddm.ddm_write_ordered(ctx, b, e, pairs)
             if record:
                 s1.record(stream)
                 write_ms.append((s0, s1))
@@ -286,8 +287,8 @@ def main():
             Ke = ddm.ddm_plan(ctx, dev[0], dev[1])
             b = 0
             while b < m:
-                e = ddm.ddm_chunk_end(ctx, b, cap)
-                k = ddm.ddm_write(ctx, b, e, pairs)
+                e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
+                k = ddm.ddm_write_ordered(ctx, b, e, pairs)
                 o = 0
                 while o < k:
                     c = min(stage.shape[0], k - o)
@@ -342,7 +343,7 @@ def main():
         "queries_per_s": m * args.steps * world / t_job,
         "p50_ms": float(np.percentile(step_ms, 50)),
         "p99_ms": float(np.percentile(step_ms, 99)),
-        "roofline": {"bound": "hbm", "kernel": "k_packets<write> (ddm_write)",
+        "roofline": {"bound": "hbm", "kernel": "k_packets<write> (ddm_write_ordered)",
                      "achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": write_gbs / hbm_peak, "traffic": None,
                      "peak_source": peak_src,

@@ -166,6 +166,33 @@ int ddm_write(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end,
 int ddm_chunk_end(ddm_ctx *ctx, uint32_t upd_begin, uint64_t capacity,
                   uint32_t *upd_end, void *stream);
 
+/* Plan order.  The counting pass runs the updates in a spatial order (the
+ * same order as the tree, so that the 32 queries of a warp lie close
+ * together).  Writing ranges of that order keeps every chunk's queries
+ * dense, which makes chunked output cheaper than update-id ranges.
+ *  order[m]           (optional, device) update id at each plan position;
+ *  order_offsets[m+1] (optional, device) exclusive prefix of the counts in
+ *                     plan order: position p's pairs are
+ *                     [order_offsets[p], order_offsets[p+1]) of an output laid
+ *                     out in plan order.
+ * Enqueued on `stream`; no synchronisation.  DDM_ERR_STATE without a plan. */
+int ddm_plan_order(ddm_ctx *ctx, uint32_t *order, uint64_t *order_offsets, void *stream);
+
+/* Write the pairs of plan positions pos_begin <= p < pos_end into
+ * pairs[0 .. order_offsets[pos_end] - order_offsets[pos_begin]), grouped by
+ * update in plan order (each update's pairs in tree order).  *k_out = that
+ * count; DDM_ERR_CAPACITY (nothing written) if it exceeds capacity.
+ * Synchronises `stream`.  Errors as ddm_write. */
+int ddm_write_ordered(ddm_ctx *ctx, uint32_t pos_begin, uint32_t pos_end,
+                      ddm_pair *pairs, uint64_t capacity, uint64_t *k_out, void *stream);
+
+/* Chunk planning for ddm_write_ordered: *pos_end = the largest e <= m such
+ * that the pairs of plan positions [pos_begin, e) fit in `capacity`;
+ * DDM_ERR_CAPACITY with *pos_end = pos_begin when position pos_begin alone
+ * does not fit.  Synchronises `stream`. */
+int ddm_chunk_end_ordered(ddm_ctx *ctx, uint32_t pos_begin, uint64_t capacity,
+                          uint32_t *pos_end, void *stream);
+
 /* ---------------------------------------------------------------------- */
 /* Introspection of the built tree (for checking intermediate results)     */
 /* ---------------------------------------------------------------------- */

@@ -53,6 +53,9 @@ SIGNATURES = {
     "ddm_plan": (_i, [_vp, _vp, _vp, _u32, _u32, _vp, _pu64, _vp]),
     "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
+    "ddm_plan_order": (_i, [_vp, _vp, _vp, _vp]),
+    "ddm_write_ordered": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
+    "ddm_chunk_end_ordered": (_i, [_vp, _u32, _u64, _pu32, _vp]),
     "ddm_tree_shape": (_i, [_vp, _pi, _pu32, _pu32]),
     "ddm_tree_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ddm_debug_set_alloc_limit": (_i, [_vp, _u64]),
@@ -195,6 +198,27 @@ def ddm_chunk_end(ctx: int, upd_begin: int, capacity: int, stream=None) -> int:
     e = ctypes.c_uint32(0)
     rc = lib().ddm_chunk_end(ctx, upd_begin, capacity, ctypes.byref(e), _stream(stream))
     _check(rc, "ddm_chunk_end", e.value)
+    return e.value
+
+
+def ddm_plan_order(ctx: int, order=None, order_offsets=None, stream=None) -> None:
+    _check(lib().ddm_plan_order(ctx, _ptr(order), _ptr(order_offsets), _stream(stream)),
+           "ddm_plan_order")
+
+
+def ddm_write_ordered(ctx: int, pos_begin: int, pos_end: int, pairs, stream=None) -> int:
+    cap = 0 if pairs is None else pairs.shape[0]
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_write_ordered(ctx, pos_begin, pos_end, _ptr(pairs), cap, ctypes.byref(k),
+                                 _stream(stream))
+    _check(rc, "ddm_write_ordered", k.value)
+    return k.value
+
+
+def ddm_chunk_end_ordered(ctx: int, pos_begin: int, capacity: int, stream=None) -> int:
+    e = ctypes.c_uint32(0)
+    rc = lib().ddm_chunk_end_ordered(ctx, pos_begin, capacity, ctypes.byref(e), _stream(stream))
+    _check(rc, "ddm_chunk_end_ordered", e.value)
     return e.value
 
 

@@ -38,7 +38,7 @@ struct ddm_ctx {
   // tree
   DevBuf e, sid, nodes;
   // plan: sorted updates, per-update counts and offsets
-  DevBuf qe, qid, counts, offsets, sums, work;
+  DevBuf qe, qid, counts, counts_pos, offsets, pos_offsets, sums, work;
   // range selection for ddm_write over a sub-range of updates
   DevBuf sel_offs, sel_list;
 
@@ -221,6 +221,7 @@ QueryView query_view(ddm_ctx* c) {
   q.qe = static_cast<const float2*>(c->qe.p);
   q.qid = static_cast<const uint32_t*>(c->qid.p);
   q.list = nullptr;
+  q.first = 0;
   q.nq = c->m;
   return q;
 }
@@ -231,13 +232,17 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   c->planned = false;
   const int d = c->tree.d;
   DDM_TRY(ensure(c, c->counts, sizeof(uint32_t) * (m ? m : 1)));
+  DDM_TRY(ensure(c, c->counts_pos, sizeof(uint32_t) * (m ? m : 1)));
   DDM_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * ((size_t)m + 1)));
+  DDM_TRY(ensure(c, c->pos_offsets, sizeof(unsigned long long) * ((size_t)m + 1)));
   DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * ((size_t)m / kScanTile + 2)));
   DDM_TRY(ensure(c, c->work, sizeof(uint32_t)));
   DDM_TRY(ensure(c, c->qe, sizeof(float2) * (size_t)d * (m ? m : 1)));
   DDM_TRY(ensure(c, c->qid, sizeof(uint32_t) * (m ? m : 1)));
   auto* counts = static_cast<uint32_t*>(c->counts.p);
+  auto* counts_pos = static_cast<uint32_t*>(c->counts_pos.p);
   auto* offsets = static_cast<unsigned long long*>(c->offsets.p);
+  auto* pos_offsets = static_cast<unsigned long long*>(c->pos_offsets.p);
   c->m = m;
   if (m > 0) {
     int cur = 0;
@@ -246,13 +251,16 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
                            static_cast<float2*>(c->qe.p), static_cast<uint32_t*>(c->qid.p), c->sms,
                            s));
     if (c->tree.n > 0) {
-      DDM_CUDA(launch_count(c->tree, query_view(c), flags, counts,
+      DDM_CUDA(launch_count(c->tree, query_view(c), flags, counts, counts_pos,
                             static_cast<uint32_t*>(c->work.p), c->sms, s));
     } else {
       DDM_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * m, s));
+      DDM_CUDA(cudaMemsetAsync(counts_pos, 0, sizeof(uint32_t) * m, s));
     }
   }
-  DDM_CUDA(launch_scan(counts, m, offsets, static_cast<unsigned long long*>(c->sums.p), c->st_dev, s));
+  auto* sums = static_cast<unsigned long long*>(c->sums.p);
+  DDM_CUDA(launch_scan(counts_pos, m, pos_offsets, sums, nullptr, s));
+  DDM_CUDA(launch_scan(counts, m, offsets, sums, c->st_dev, s));
   c->ulo = ulo;
   c->uhi = uhi;
   c->flags = flags;
@@ -260,6 +268,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   return DDM_OK;
 }
 
+// Write pass for updates with ids in [begin, end), laid out by update id.
 int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
                 cudaStream_t s) {
   if (end > begin && c->tree.n > 0) {
@@ -274,9 +283,37 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
       q.list = static_cast<const uint32_t*>(c->sel_list.p);
       q.nq = end - begin;
     }
-    DDM_CUDA(launch_write(c->tree, q, c->flags, begin, end,
-                          static_cast<const unsigned long long*>(c->offsets.p), pairs, capacity,
-                          static_cast<uint32_t*>(c->work.p), c->st_dev, c->sms, s));
+    WriteView w{};
+    w.start = static_cast<const unsigned long long*>(c->offsets.p);
+    w.by_pos = false;
+    w.b_idx = begin;
+    w.e_idx = end;
+    w.pairs = pairs;
+    w.capacity = capacity;
+    DDM_CUDA(launch_write(c->tree, q, c->flags, w, static_cast<uint32_t*>(c->work.p), c->st_dev,
+                          c->sms, s));
+  } else {
+    DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
+  }
+  return DDM_OK;
+}
+
+// Write pass for the plan positions [pb, pe), laid out in plan order.
+int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, uint64_t capacity,
+                        cudaStream_t s) {
+  if (pe > pb && c->tree.n > 0) {
+    QueryView q = query_view(c);
+    q.first = pb;
+    q.nq = pe - pb;
+    WriteView w{};
+    w.start = static_cast<const unsigned long long*>(c->pos_offsets.p);
+    w.by_pos = true;
+    w.b_idx = pb;
+    w.e_idx = pe;
+    w.pairs = pairs;
+    w.capacity = capacity;
+    DDM_CUDA(launch_write(c->tree, q, c->flags, w, static_cast<uint32_t*>(c->work.p), c->st_dev,
+                          c->sms, s));
   } else {
     DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
   }
@@ -336,7 +373,8 @@ int ddm_destroy(ddm_ctx* c) {
   cudaDeviceSynchronize();
   for (DevBuf* b : {&c->keys[0], &c->keys[1], &c->vals[0], &c->vals[1], &c->hist, &c->lookback,
                     &c->counters, &c->e, &c->sid, &c->nodes, &c->qe, &c->qid, &c->counts,
-                    &c->offsets, &c->sums, &c->work, &c->sel_offs, &c->sel_list})
+                    &c->counts_pos, &c->offsets, &c->pos_offsets, &c->sums, &c->work,
+                    &c->sel_offs, &c->sel_list})
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -412,6 +450,52 @@ int ddm_chunk_end(ddm_ctx* c, uint32_t begin, uint64_t capacity, uint32_t* upd_e
   DDM_TRY(sync_status(c, s));
   *upd_end = (uint32_t)c->st_host->aux;
   if (*upd_end == begin && begin < c->m) return DDM_ERR_CAPACITY;
+  return DDM_OK;
+}
+
+int ddm_write_ordered(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, ddm_pair* pairs,
+                      uint64_t capacity, uint64_t* k_out, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  if (pos_begin > pos_end || pos_end > c->m || (pos_end > pos_begin && !pairs)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(write_ordered_async(c, pos_begin, pos_end, pairs, capacity, s));
+  DDM_TRY(sync_status(c, s));
+  if (k_out) *k_out = c->st_host->K;
+  return status_code(*c->st_host);
+}
+
+int ddm_chunk_end_ordered(ddm_ctx* c, uint32_t pos_begin, uint64_t capacity, uint32_t* pos_end,
+                          void* stream) {
+  if (!c || !pos_end) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  if (pos_begin > c->m) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_CUDA(launch_chunk_end(static_cast<const unsigned long long*>(c->pos_offsets.p), c->m,
+                            pos_begin, capacity, c->st_dev, s));
+  DDM_TRY(sync_status(c, s));
+  *pos_end = (uint32_t)c->st_host->aux;
+  if (*pos_end == pos_begin && pos_begin < c->m) return DDM_ERR_CAPACITY;
+  return DDM_OK;
+}
+
+int ddm_plan_order(ddm_ctx* c, uint32_t* order, uint64_t* order_offsets, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (order && c->m)
+    DDM_CUDA(cudaMemcpyAsync(order, c->qid.p, sizeof(uint32_t) * c->m, cudaMemcpyDeviceToDevice, s));
+  if (order_offsets)
+    DDM_CUDA(cudaMemcpyAsync(order_offsets, c->pos_offsets.p,
+                             sizeof(unsigned long long) * ((size_t)c->m + 1),
+                             cudaMemcpyDeviceToDevice, s));
   return DDM_OK;
 }
 

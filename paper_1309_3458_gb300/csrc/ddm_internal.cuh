@@ -51,7 +51,19 @@ struct QueryView {
   const float2* qe;               // [d][m] (lo, hi) per dimension, sorted order
   const uint32_t* qid;            // [m] update id per sorted position
   const uint32_t* list;           // optional subset of sorted positions (ranges)
-  uint32_t nq;                    // number of queries to run (m, or |list|)
+  uint32_t first;                 // without list: run positions first .. first+nq-1
+  uint32_t nq;                    // number of queries to run
+};
+
+// Where the write pass puts each query's pairs: query j's pairs start at
+// start[key] - start[b_idx] in `pairs`, key = its update id (by_pos false) or
+// its sorted position (by_pos true); start[e_idx] - start[b_idx] pairs in all.
+struct WriteView {
+  const unsigned long long* start;
+  bool by_pos;
+  uint32_t b_idx, e_idx;
+  ddm_pair* pairs;
+  unsigned long long capacity;
 };
 
 // Order-preserving map from float to uint32 (IEEE order; -0 maps like +0).
@@ -111,12 +123,11 @@ cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const fl
 cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s);
 
 // ---- ddm_query.cu ---------------------------------------------------------
+// counts[update id] (and counts_pos[sorted position], if not null).
 cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                         uint32_t* work, int sms, cudaStream_t s);
-cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t begin,
-                         uint32_t end, const unsigned long long* offsets, ddm_pair* pairs,
-                         unsigned long long capacity, uint32_t* work, Status* st, int sms,
-                         cudaStream_t s);
+                         uint32_t* counts_pos, uint32_t* work, int sms, cudaStream_t s);
+cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, const WriteView& w,
+                         uint32_t* work, Status* st, int sms, cudaStream_t s);
 
 // ---- ddm_scan.cu ----------------------------------------------------------
 constexpr int kScanTile = 4096;

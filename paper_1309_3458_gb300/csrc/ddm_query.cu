@@ -20,9 +20,10 @@
 //     query's matches in the leaf.
 //
 // The count pass adds up matches per update; the write pass stores
-// (update, subscription) pairs from the update's offset in the exclusive
-// scan of the counts.  Both walk the same leaves in the same order, so the
-// write pass reproduces the counted pairs exactly, in tree order.
+// (update, subscription) pairs from each update's output offset.  Both walk
+// the same leaves in the same order, so the write pass reproduces the
+// counted pairs exactly, in tree order.  Predicates are combined with
+// bitwise ANDs so the per-query test has no branches.
 #include <cfloat>
 
 #include "ddm_internal.cuh"
@@ -59,10 +60,8 @@ __device__ __forceinline__ float warp_min(float v) {
 // D > 0: compile-time dimension count; D == 0: runtime d (up to 8).
 template <int D, bool OPEN, bool WRITE>
 __global__ void __launch_bounds__(kThreads)
-k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
-          const unsigned long long* __restrict__ offsets, ddm_pair* __restrict__ pairs,
-          unsigned long long capacity, uint32_t begin, uint32_t end, uint32_t* __restrict__ work,
-          Status* __restrict__ st) {
+k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __restrict__ counts_pos,
+          WriteView w, uint32_t* __restrict__ work, Status* __restrict__ st) {
   constexpr int DM = D > 0 ? D : DDM_MAX_DIMS;
   const int d = D > 0 ? D : t.d;
   __shared__ float2 s_q[kWarps][DM][32];
@@ -72,13 +71,13 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
 
   unsigned long long base0 = 0;
   if (WRITE) {
-    base0 = offsets[begin];
-    const unsigned long long need = offsets[end] - base0;
+    base0 = w.start[w.b_idx];
+    const unsigned long long need = w.start[w.e_idx] - base0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
       st->K = need;
-      if (need > capacity) atomicOr(&st->err, kErrCapacity);
+      if (need > w.capacity) atomicOr(&st->err, kErrCapacity);
     }
-    if (need > capacity) return;
+    if (need > w.capacity) return;
   }
 
   const uint32_t npk = (q.nq + 31u) >> 5;
@@ -93,7 +92,7 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
     const bool valid = idx < q.nq;
     uint32_t pos = 0, Q = 0;
     if (valid) {
-      pos = q.list ? q.list[idx] : idx;
+      pos = q.list ? q.list[idx] : q.first + idx;
       Q = q.qid[pos];
     }
     float ql[DM], qh[DM], gl[DM], gh[DM];
@@ -109,27 +108,24 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
       }
     }
     uint32_t cnt = 0;
-    unsigned long long out = 0, lim = 0;
-    if (WRITE && valid) {
-      out = offsets[Q] - base0;
-      lim = offsets[Q + 1] - base0;
-    }
+    unsigned long long out = 0;
+    if (WRITE && valid) out = w.start[w.by_pos ? pos : Q] - base0;
     __syncwarp();
 
     // Test the 32 level-1 nodes (leaves) from g1 on against the packet box,
     // then run the packet's queries over each surviving leaf.
     auto leaves = [&](uint32_t g1) {
       const uint32_t c = g1 + lane;
+      const bool cv = c < t.cnt[1];
       float bl[DM], bh[DM];
-      bool ok = c < t.cnt[1];
+      bool ok = cv;
 #pragma unroll
       for (int k = 0; k < DM; ++k) {
         if (k < d) {
-          const float2 v = c < t.cnt[1] ? t.nodes[k * total + t.off[1] + c]
-                                        : make_float2(INFINITY, -INFINITY);
+          const float2 v = cv ? t.nodes[k * total + t.off[1] + c] : make_float2(INFINITY, -INFINITY);
           bl[k] = v.x;
           bh[k] = v.y;
-          ok = ok && le<OPEN>(v.x, gh[k]) && le<OPEN>(gl[k], v.y);
+          ok = ok & le<OPEN>(v.x, gh[k]) & le<OPEN>(gl[k], v.y);
         }
       }
       uint32_t lm = __ballot_sync(0xffffffffu, ok);
@@ -143,7 +139,7 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
           if (k < d) {
             const float a = __shfl_sync(0xffffffffu, bl[k], cl);
             const float b = __shfl_sync(0xffffffffu, bh[k], cl);
-            qok = qok && le<OPEN>(a, qh[k]) && le<OPEN>(ql[k], b);
+            qok = qok & le<OPEN>(a, qh[k]) & le<OPEN>(ql[k], b);
           }
         }
         uint32_t qm = __ballot_sync(0xffffffffu, qok);
@@ -164,24 +160,23 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
           for (int k = 0; k < DM; ++k) {
             if (k < d) {
               const float2 b = s_q[wib][k][qq];
-              hit = hit && le<OPEN>(ev[k].x, b.y) && le<OPEN>(b.x, ev[k].y);
+              hit = hit & le<OPEN>(ev[k].x, b.y) & le<OPEN>(b.x, ev[k].y);
             }
           }
           const uint32_t hb = __ballot_sync(0xffffffffu, hit);
           if (WRITE) {
             const unsigned long long o = __shfl_sync(0xffffffffu, out, qq);
-            const unsigned long long lq = __shfl_sync(0xffffffffu, lim, qq);
             const uint32_t Qq = __shfl_sync(0xffffffffu, Q, qq);
             if (hit) {
               const unsigned long long at = o + __popc(hb & lt);
-              if (at < lq) {
+              if (at < w.capacity) {
                 ddm_pair pr;
                 pr.upd = Qq;
                 pr.sub = my_sid;
-                pairs[at] = pr;
+                w.pairs[at] = pr;
               }
             }
-            if (lane == qq) out += __popc(hb);
+            if (lane == qq) out = o + __popc(hb);
           } else {
             if (lane == qq) cnt += __popc(hb);
           }
@@ -197,12 +192,14 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
       uint32_t mask[kMaxLevels + 1], base[kMaxLevels + 1];
       int lvl = t.L;
       {
-        bool ok = (uint32_t)lane < t.cnt[lvl];
+        const bool cv = (uint32_t)lane < t.cnt[lvl];
+        bool ok = cv;
 #pragma unroll
         for (int k = 0; k < DM; ++k) {
-          if (k < d && ok) {
-            const float2 v = t.nodes[k * total + t.off[lvl] + lane];
-            ok = le<OPEN>(v.x, gh[k]) && le<OPEN>(gl[k], v.y);
+          if (k < d) {
+            const float2 v = cv ? t.nodes[k * total + t.off[lvl] + lane]
+                                : make_float2(INFINITY, -INFINITY);
+            ok = ok & le<OPEN>(v.x, gh[k]) & le<OPEN>(gl[k], v.y);
           }
         }
         mask[lvl] = __ballot_sync(0xffffffffu, ok);
@@ -221,12 +218,14 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
           leaves(g * 32u);
         } else {
           const uint32_t ch = g * 32u + lane;
-          bool ok = ch < t.cnt[lvl - 1];
+          const bool cv = ch < t.cnt[lvl - 1];
+          bool ok = cv;
 #pragma unroll
           for (int k = 0; k < DM; ++k) {
-            if (k < d && ok) {
-              const float2 v = t.nodes[k * total + t.off[lvl - 1] + ch];
-              ok = le<OPEN>(v.x, gh[k]) && le<OPEN>(gl[k], v.y);
+            if (k < d) {
+              const float2 v = cv ? t.nodes[k * total + t.off[lvl - 1] + ch]
+                                  : make_float2(INFINITY, -INFINITY);
+              ok = ok & le<OPEN>(v.x, gh[k]) & le<OPEN>(gl[k], v.y);
             }
           }
           --lvl;
@@ -235,15 +234,17 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts,
         }
       }
     }
-    if (!WRITE && valid) counts[Q] = cnt;
+    if (!WRITE && valid) {
+      counts[Q] = cnt;
+      if (counts_pos) counts_pos[pos] = cnt;
+    }
   }
 }
 
 template <bool WRITE>
-cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t begin,
-                           uint32_t end, uint32_t* counts, const unsigned long long* offsets,
-                           ddm_pair* pairs, unsigned long long capacity, uint32_t* work,
-                           Status* st, int sms, cudaStream_t s) {
+cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
+                           uint32_t* counts_pos, const WriteView& w, uint32_t* work, Status* st,
+                           int sms, cudaStream_t s) {
   if (q.nq == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
@@ -252,9 +253,8 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags
   uint32_t blocks = (packets + kWarps - 1) / kWarps;
   const uint32_t cap = (uint32_t)sms * 8u;
   if (blocks > cap) blocks = cap;
-#define DDM_LAUNCH(DD, OP)                                                                    \
-  k_packets<DD, OP, WRITE><<<blocks, kThreads, 0, s>>>(t, q, counts, offsets, pairs, capacity, \
-                                                        begin, end, work, st)
+#define DDM_LAUNCH(DD, OP) \
+  k_packets<DD, OP, WRITE><<<blocks, kThreads, 0, s>>>(t, q, counts, counts_pos, w, work, st)
   switch (t.d) {
     case 1: open ? DDM_LAUNCH(1, true) : DDM_LAUNCH(1, false); break;
     case 2: open ? DDM_LAUNCH(2, true) : DDM_LAUNCH(2, false); break;
@@ -269,17 +269,14 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags
 }  // namespace
 
 cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                         uint32_t* work, int sms, cudaStream_t s) {
-  return launch_packets<false>(t, q, flags, 0, 0, counts, nullptr, nullptr, 0, work, nullptr, sms,
-                               s);
+                         uint32_t* counts_pos, uint32_t* work, int sms, cudaStream_t s) {
+  WriteView w{};
+  return launch_packets<false>(t, q, flags, counts, counts_pos, w, work, nullptr, sms, s);
 }
 
-cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t begin,
-                         uint32_t end, const unsigned long long* offsets, ddm_pair* pairs,
-                         unsigned long long capacity, uint32_t* work, Status* st, int sms,
-                         cudaStream_t s) {
-  return launch_packets<true>(t, q, flags, begin, end, nullptr, offsets, pairs, capacity, work, st,
-                              sms, s);
+cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, const WriteView& w,
+                         uint32_t* work, Status* st, int sms, cudaStream_t s) {
+  return launch_packets<true>(t, q, flags, nullptr, nullptr, w, work, st, sms, s);
 }
 
 }  // namespace ddm

@@ -225,6 +225,43 @@ def test_staged_chunks_reproduce_full_output(ctx):
     assert np.array_equal(sl[:, 1], ps[off[1234]:off[4321]])
 
 
+def test_ordered_chunks_cover_the_same_pairs(ctx):
+    import torch
+    arrays = W.clustered_lognormal(40000, 30000, d=3, alpha=100.0, seed=12)
+    K, pu, ps = gpu_match(ctx, arrays)
+    U = to_dev(arrays)
+    ddm.ddm_build(ctx, U[2], U[3])
+    m = 30000
+    off = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    assert ddm.ddm_plan(ctx, U[0], U[1], offsets=off) == K
+    order = torch.empty(m, dtype=torch.int32, device="cuda")
+    ooff = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    ddm.ddm_plan_order(ctx, order, ooff)
+    torch.cuda.synchronize()
+    off, order, ooff = off.cpu().numpy(), order.cpu().numpy(), ooff.cpu().numpy()
+    assert np.array_equal(np.sort(order), np.arange(m))
+    assert ooff[0] == 0 and ooff[-1] == K
+    assert np.array_equal(np.diff(ooff), np.diff(off)[order])
+    cap = K // 5 + 1
+    buf = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
+    got, b = [], 0
+    while b < m:
+        e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
+        assert e > b and ooff[e] - ooff[b] <= cap and (e == m or ooff[e + 1] - ooff[b] > cap)
+        k = ddm.ddm_write_ordered(ctx, b, e, buf)
+        assert k == ooff[e] - ooff[b]
+        got.append(buf[:k].cpu().numpy().view(np.uint32).copy())
+        b = e
+    got = np.concatenate(got)
+    # grouped by update in plan order, same pairs as the one-shot match
+    assert np.array_equal(got[:, 0], np.repeat(order, np.diff(ooff)).astype(np.uint32))
+    assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(pu, ps)))
+    # each update's list is identical (same order) in both layouts
+    j = int(order[len(order) // 2])
+    sel = got[:, 0] == j
+    assert np.array_equal(got[sel, 1], ps[off[j]:off[j + 1]])
+
+
 # --- error paths -------------------------------------------------------------
 
 def test_invalid_extents(ctx):
