@@ -48,7 +48,9 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--config", default=DEFAULT_CONFIG)
-    ap.add_argument("--chunk-gb", type=float, default=64.0, help="device pair buffer (GB)")
+    ap.add_argument("--scale", type=float, default=1.0,
+                    help="shrink n and m (profiling a small case of the same workload)")
+    ap.add_argument("--chunk-gb", type=float, default=32.0, help="device pair buffer (GB)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--stage-gb", type=float, default=2.0, help="pinned host staging (GB)")
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
@@ -64,9 +66,9 @@ def dist():
     return rank, world, local
 
 
-def workload(name, rank):
+def workload(name, rank, scale=1.0):
     from paper_1309_3458_gb300 import workloads as W
-    arrays = W.make(name)
+    arrays = W.make(name, scale)
     if rank:
         # a different update set per rank, same subscriptions
         c = dict(W.CONFIGS[name])
@@ -169,7 +171,7 @@ def cpu_oracle_sample(arrays, budget_s):
 def reference_arm(args, rank, world):
     if rank != 0:
         return
-    arrays = workload(args.config, 0)
+    arrays = workload(args.config, 0, args.scale)
     res = []
     for _ in range(args.warmup + args.steps):
         res.append(cpu_oracle_sample(arrays, args.cpu_seconds / max(1, args.steps)))
@@ -206,7 +208,7 @@ def main():
         if world > 1:
             tdist.barrier()
 
-    arrays = workload(args.config, rank)
+    arrays = workload(args.config, rank, args.scale)
     d, m = arrays[0].shape
     n = arrays[2].shape[1]
     dev = tuple(torch.from_numpy(a).cuda() for a in arrays)
@@ -216,13 +218,16 @@ def main():
     stream = torch.cuda.current_stream()
 
     write_ms, write_bytes = [], []
+    chunks = [0]
 
     def step(record=False):
         ddm.ddm_build(ctx, dev[2], dev[3])
         K = ddm.ddm_plan(ctx, dev[0], dev[1])
         b = 0
+        chunks[0] = 0
         while b < m:
             e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
+            chunks[0] += 1
             if record:
                 s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 s0.record(stream)
@@ -337,9 +342,11 @@ def main():
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": args.config, "d": d, "n_sub": n, "m_upd": m, "K": K,
-                   "chunk_pairs": cap, "l2": "inputs (%.0f MB) larger than L2" % (
-                       sum(a.nbytes for a in arrays) / 1e6)},
+        "config": {"workload": args.config if args.scale == 1.0 else f"{args.config}@{args.scale}",
+                   "d": d, "n_sub": n, "m_upd": m, "K": K,
+                   "chunk_pairs": cap, "chunks": chunks[0], "l2": "inputs %.0f MB (%s L2, no flush)" % (
+                       sum(a.nbytes for a in arrays) / 1e6,
+                       "larger than" if sum(a.nbytes for a in arrays) > 129e6 else "within")},
         "queries_per_s": m * args.steps * world / t_job,
         "p50_ms": float(np.percentile(step_ms, 50)),
         "p99_ms": float(np.percentile(step_ms, 99)),

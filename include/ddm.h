@@ -216,6 +216,17 @@ int ddm_tree_shape(ddm_ctx *ctx, int *levels, uint32_t *counts, uint32_t *total)
 int ddm_tree_export(ddm_ctx *ctx, uint32_t *order, float *node_lo, float *node_hi,
                     void *stream);
 
+/* Record budget of the write pass.  While counting, ddm_plan (and the
+ * one-shot calls) can keep a compact record of every (update, leaf) test
+ * that found pairs -- 8 bytes per record, about one record per 6-8 pairs --
+ * so that the write pass expands the records instead of walking the tree a
+ * second time.  The records live in a context arena of at most `bytes`
+ * (default: a quarter of the device's memory); the arena is sized from what
+ * the previous count pass needed, so the first plan on a large workload may
+ * run out of room and fall back to walking.  Results are identical either
+ * way.  0 turns recording off.  DDM_ERR_ARG for a NULL context. */
+int ddm_set_replay_budget(ddm_ctx *ctx, uint64_t bytes);
+
 /* Testing aid: make device workspace allocations that would bring the
  * context's total above `bytes` fail with DDM_ERR_NOMEM (0 = no limit). */
 int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);

@@ -59,6 +59,7 @@ SIGNATURES = {
     "ddm_tree_shape": (_i, [_vp, _pi, _pu32, _pu32]),
     "ddm_tree_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ddm_debug_set_alloc_limit": (_i, [_vp, _u64]),
+    "ddm_set_replay_budget": (_i, [_vp, _u64]),
     "ddm_debug_launch_count": (_u64, []),
     "ddm_scan_counts_noalloc": (_i, [_vp, _u32, _vp, _vp]),
 }
@@ -233,6 +234,10 @@ def ddm_tree_shape(ctx: int) -> Tuple[int, Sequence[int], int]:
 def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=None) -> None:
     _check(lib().ddm_tree_export(ctx, _ptr(order), _ptr(node_lo), _ptr(node_hi),
                                  _stream(stream)), "ddm_tree_export")
+
+
+def ddm_set_replay_budget(ctx: int, nbytes: int) -> None:
+    _check(lib().ddm_set_replay_budget(ctx, nbytes), "ddm_set_replay_budget")
 
 
 def ddm_debug_set_alloc_limit(ctx: int, nbytes: int) -> None:

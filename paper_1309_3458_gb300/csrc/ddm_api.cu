@@ -41,6 +41,13 @@ struct ddm_ctx {
   DevBuf qe, qid, counts, counts_pos, offsets, pos_offsets, sums, work;
   // range selection for ddm_write over a sub-range of updates
   DevBuf sel_offs, sel_list;
+  // replay records of the count pass
+  DevBuf rec, blk_next, blk_count, blk_pkt, blk_base, pkt_first, pkt_nblk, pkt_off, blk_list,
+      blk_counter;
+  uint64_t replay_budget = 0;   // bytes; 0 = never record
+  uint32_t rec_blocks = 0;      // blocks of the current arena
+  uint32_t rec_hint = 0;        // blocks the last count pass asked for
+  RecordArena arena{};          // arena of the current plan (max_blocks 0 = none)
 
   bool built = false;
   TreeView tree{};
@@ -228,7 +235,7 @@ QueryView query_view(ddm_ctx* c) {
 
 // Validate U, sort it, count per update, scan (no host synchronisation).
 int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_t flags,
-               cudaStream_t s) {
+               bool record, cudaStream_t s) {
   c->planned = false;
   const int d = c->tree.d;
   DDM_TRY(ensure(c, c->counts, sizeof(uint32_t) * (m ? m : 1)));
@@ -244,6 +251,39 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   auto* offsets = static_cast<unsigned long long*>(c->offsets.p);
   auto* pos_offsets = static_cast<unsigned long long*>(c->pos_offsets.p);
   c->m = m;
+  c->arena = RecordArena{};
+  if (record && m > 0 && c->tree.n > 0 && c->replay_budget > 0) {
+    const uint32_t packets = (m + 31) / 32;
+    // bytes per block: records, next/count/packet/list entries, 32 base counts
+    const uint64_t per_block = (uint64_t)kRecBlock * sizeof(uint2) + 36 * sizeof(uint32_t);
+    uint64_t want = c->rec_hint ? (uint64_t)c->rec_hint + c->rec_hint / 8 + 64 : 2ull * packets;
+    const uint64_t cap_blocks = c->replay_budget / per_block;
+    if (want > cap_blocks) want = cap_blocks;
+    if (want > 0xfffffff0ull) want = 0xfffffff0ull;
+    if (want > 0 && ensure(c, c->rec, (size_t)want * kRecBlock * sizeof(uint2)) == DDM_OK &&
+        ensure(c, c->blk_next, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->blk_count, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->blk_pkt, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->blk_base, (size_t)want * 32 * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->blk_list, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->pkt_first, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->pkt_nblk, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->pkt_off, ((size_t)packets + 1) * sizeof(unsigned long long)) == DDM_OK &&
+        ensure(c, c->blk_counter, 2 * sizeof(uint32_t)) == DDM_OK) {
+      c->arena.rec = static_cast<uint2*>(c->rec.p);
+      c->arena.blk_next = static_cast<uint32_t*>(c->blk_next.p);
+      c->arena.blk_count = static_cast<uint32_t*>(c->blk_count.p);
+      c->arena.pkt_first = static_cast<uint32_t*>(c->pkt_first.p);
+      c->arena.blk_pkt = static_cast<uint32_t*>(c->blk_pkt.p);
+      c->arena.blk_base = static_cast<uint32_t*>(c->blk_base.p);
+      c->arena.blk_list = static_cast<uint32_t*>(c->blk_list.p);
+      c->arena.pkt_nblk = static_cast<uint32_t*>(c->pkt_nblk.p);
+      c->arena.pkt_off = static_cast<unsigned long long*>(c->pkt_off.p);
+      c->arena.blk_counter = static_cast<uint32_t*>(c->blk_counter.p);
+      c->arena.max_blocks = (uint32_t)want;
+      DDM_CUDA(cudaMemsetAsync(c->blk_counter.p, 0, 2 * sizeof(uint32_t), s));
+    }
+  }
   if (m > 0) {
     int cur = 0;
     DDM_TRY(order_set(c, d, ulo, uhi, m, false, &cur, s));
@@ -251,7 +291,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
                            static_cast<float2*>(c->qe.p), static_cast<uint32_t*>(c->qid.p), c->sms,
                            s));
     if (c->tree.n > 0) {
-      DDM_CUDA(launch_count(c->tree, query_view(c), flags, counts, counts_pos,
+      DDM_CUDA(launch_count(c->tree, query_view(c), flags, counts, counts_pos, c->arena,
                             static_cast<uint32_t*>(c->work.p), c->sms, s));
     } else {
       DDM_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * m, s));
@@ -261,6 +301,14 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   auto* sums = static_cast<unsigned long long*>(c->sums.p);
   DDM_CUDA(launch_scan(counts_pos, m, pos_offsets, sums, nullptr, s));
   DDM_CUDA(launch_scan(counts, m, offsets, sums, c->st_dev, s));
+  if (c->arena.max_blocks) {  // plan-order list of the record blocks
+    const uint32_t packets = (m + 31) / 32;
+    DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets, c->arena.pkt_off, sums, nullptr, s));
+    DDM_CUDA(launch_block_list(c->arena, packets, s));
+  }
+  if (c->arena.max_blocks)  // blocks the count pass asked for, read back with the status
+    DDM_CUDA(cudaMemcpyAsync(&c->st_dev->aux, static_cast<uint32_t*>(c->blk_counter.p) + 1,
+                             sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   c->ulo = ulo;
   c->uhi = uhi;
   c->flags = flags;
@@ -290,8 +338,13 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
     w.e_idx = end;
     w.pairs = pairs;
     w.capacity = capacity;
-    DDM_CUDA(launch_write(c->tree, q, c->flags, w, static_cast<uint32_t*>(c->work.p), c->st_dev,
-                          c->sms, s));
+    auto* work = static_cast<uint32_t*>(c->work.p);
+    if (c->arena.max_blocks) {
+      const bool full = begin == 0 && end == c->m;
+      DDM_CUDA(launch_replay(c->tree, query_view(c), c->arena, w, 0, (c->m + 31) / 32, 0, c->m,
+                             !full, begin, end, work, c->st_dev, c->sms, s));
+    }
+    DDM_CUDA(launch_write(c->tree, q, c->flags, w, c->arena, work, c->st_dev, c->sms, s));
   } else {
     DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
   }
@@ -312,8 +365,11 @@ int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, u
     w.e_idx = pe;
     w.pairs = pairs;
     w.capacity = capacity;
-    DDM_CUDA(launch_write(c->tree, q, c->flags, w, static_cast<uint32_t*>(c->work.p), c->st_dev,
-                          c->sms, s));
+    auto* work = static_cast<uint32_t*>(c->work.p);
+    if (c->arena.max_blocks)
+      DDM_CUDA(launch_replay(c->tree, q, c->arena, w, pb / 32, (pe + 31) / 32, pb, pe, false, 0, 0,
+                             work, c->st_dev, c->sms, s));
+    DDM_CUDA(launch_write(c->tree, q, c->flags, w, c->arena, work, c->st_dev, c->sms, s));
   } else {
     DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
   }
@@ -356,6 +412,11 @@ int ddm_create(ddm_ctx** out, int device) {
   ddm_ctx* c = new (std::nothrow) ddm_ctx();
   if (!c) return DDM_ERR_NOMEM;
   c->device = device;
+  {
+    size_t free_b = 0, total_b = 0;
+    if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) c->replay_budget = total_b / 4;
+    cudaGetLastError();
+  }
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&c->st_dev, sizeof(Status)) != cudaSuccess ||
       cudaMallocHost(&c->st_host, sizeof(Status)) != cudaSuccess) {
@@ -374,11 +435,20 @@ int ddm_destroy(ddm_ctx* c) {
   for (DevBuf* b : {&c->keys[0], &c->keys[1], &c->vals[0], &c->vals[1], &c->hist, &c->lookback,
                     &c->counters, &c->e, &c->sid, &c->nodes, &c->qe, &c->qid, &c->counts,
                     &c->counts_pos, &c->offsets, &c->pos_offsets, &c->sums, &c->work,
-                    &c->sel_offs, &c->sel_list})
+                    &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
+                    &c->blk_pkt, &c->blk_base, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
+                    &c->blk_list, &c->blk_counter})
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
   delete c;
+  return DDM_OK;
+}
+
+int ddm_set_replay_budget(ddm_ctx* c, uint64_t bytes) {
+  if (!c) return DDM_ERR_ARG;
+  c->replay_budget = bytes;
+  c->rec_hint = 0;
   return DDM_OK;
 }
 
@@ -412,11 +482,12 @@ int ddm_plan(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DDM_TRY(reset_status(c, s));
-  DDM_TRY(plan_async(c, ulo, uhi, m, flags, s));
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags, true, s));
   if (offsets)
     DDM_CUDA(cudaMemcpyAsync(offsets, c->offsets.p, sizeof(unsigned long long) * ((size_t)m + 1),
                              cudaMemcpyDeviceToDevice, s));
   DDM_TRY(sync_status(c, s));
+  if (c->arena.max_blocks) c->rec_hint = (uint32_t)c->st_host->aux;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   if (rc != DDM_OK) c->planned = false;
@@ -511,12 +582,16 @@ static int match_impl(ddm_ctx* c, int d, const float* ulo, const float* uhi, uin
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(build_async(c, d, slo, shi, n, s));
-  DDM_TRY(plan_async(c, ulo, uhi, m, flags, s));
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags, write, s));
   if (write) {
     if (end > begin && !pairs && capacity > 0) return DDM_ERR_ARG;
     DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
   }
+  if (c->arena.max_blocks)
+    DDM_CUDA(cudaMemcpyAsync(&c->st_dev->aux, static_cast<uint32_t*>(c->blk_counter.p) + 1,
+                             sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   DDM_TRY(sync_status(c, s));
+  if (c->arena.max_blocks) c->rec_hint = (uint32_t)c->st_host->aux;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   if (rc == DDM_ERR_EXTENT || rc == DDM_ERR_TIMEOUT) c->built = c->planned = false;

@@ -123,11 +123,57 @@ cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const fl
 cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s);
 
 // ---- ddm_query.cu ---------------------------------------------------------
-// counts[update id] (and counts_pos[sorted position], if not null).
+// Replay records.  While counting, every (query, leaf) test of a packet
+// that has hits is stored as one record: x = leaf << 5 | query lane,
+// y = hit mask over the leaf's 32 subscriptions.  Records of a packet are
+// kept in walk order (leaf by leaf, query lanes ascending within a leaf), in
+// a chain of fixed-size blocks taken from a shared arena.  Each block also
+// stores its packet and, per query lane, the matches the packet had before
+// the block, so every block can be expanded on its own: after counting, the
+// blocks are listed in plan order and the write pass expands any range of
+// them in parallel, instead of walking the tree again.
+constexpr uint32_t kRecBlock = 512;       // records per block (4 KiB)
+constexpr uint32_t kNoBlock = 0xffffffffu;
+struct RecordArena {
+  uint2* rec;              // [max_blocks * kRecBlock]
+  uint32_t* blk_next;      // [max_blocks] next block of the packet, or kNoBlock
+  uint32_t* blk_count;     // [max_blocks] records in the block
+  uint32_t* blk_pkt;       // [max_blocks] packet of the block
+  uint32_t* blk_base;      // [max_blocks * 32] per query lane: matches before the block
+  uint32_t* pkt_first;     // [packets] first block of each packet, or kNoBlock
+  uint32_t* pkt_nblk;      // [packets] blocks of each packet
+  unsigned long long* pkt_off;  // [packets + 1] exclusive prefix of pkt_nblk
+  uint32_t* blk_list;      // [max_blocks] blocks in plan order
+  uint32_t* blk_counter;   // [0] blocks handed out (may exceed max_blocks),
+                           // [1] blocks the whole pass needed
+  uint32_t max_blocks;     // 0: no recording
+};
+// The records of the last count pass are complete (the write pass may
+// replay them) iff recording was on and the arena did not run out.
+__device__ __forceinline__ bool records_complete(const RecordArena& ra) {
+  return ra.max_blocks > 0 && ra.blk_counter[0] <= ra.max_blocks;
+}
+
+// counts[update id] (and counts_pos[sorted position], if not null); records
+// into `ra` when ra.max_blocks > 0.
 cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                         uint32_t* counts_pos, uint32_t* work, int sms, cudaStream_t s);
+                         uint32_t* counts_pos, const RecordArena& ra, uint32_t* work, int sms,
+                         cudaStream_t s);
+// Walking write pass; it does nothing when `ra` holds complete records (the
+// replay kernel, launched next to it, writes the pairs then).
 cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, const WriteView& w,
-                         uint32_t* work, Status* st, int sms, cudaStream_t s);
+                         const RecordArena& ra, uint32_t* work, Status* st, int sms,
+                         cudaStream_t s);
+// After the count pass: blk_list = every packet's chain, packets in plan
+// order (pkt_off must already hold the prefix of pkt_nblk).
+cudaError_t launch_block_list(const RecordArena& ra, uint32_t packets, cudaStream_t s);
+// Write pass from records: packets [p0, p1) of the plan, positions [pb, pe),
+// and (when id_filter) only updates with ids in [idb, ide).  Does nothing
+// unless `ra` holds complete records.
+cudaError_t launch_replay(const TreeView& t, const QueryView& q, const RecordArena& ra,
+                          const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
+                          bool id_filter, uint32_t idb, uint32_t ide, uint32_t* work, Status* st,
+                          int sms, cudaStream_t s);
 
 // ---- ddm_scan.cu ----------------------------------------------------------
 constexpr int kScanTile = 4096;

@@ -25,6 +25,7 @@
 // counted pairs exactly, in tree order.  Predicates are combined with
 // bitwise ANDs so the per-query test has no branches.
 #include <cfloat>
+#include <type_traits>
 
 #include "ddm_internal.cuh"
 
@@ -33,6 +34,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Resident 256-thread blocks per SM the packet kernels are compiled for.
+#ifndef DDM_PACKET_MIN_BLOCKS
+#define DDM_PACKET_MIN_BLOCKS 4
+#endif
 
 template <bool OPEN>
 __device__ __forceinline__ bool le(float a, float b) {
@@ -59,18 +64,20 @@ __device__ __forceinline__ float warp_min(float v) {
 
 // D > 0: compile-time dimension count; D == 0: runtime d (up to 8).
 template <int D, bool OPEN, bool WRITE>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kThreads, DDM_PACKET_MIN_BLOCKS)
 k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __restrict__ counts_pos,
-          WriteView w, uint32_t* __restrict__ work, Status* __restrict__ st) {
+          RecordArena ra, WriteView w, uint32_t* __restrict__ work, Status* __restrict__ st) {
   constexpr int DM = D > 0 ? D : DDM_MAX_DIMS;
+  constexpr int DP = (DM + 1) / 2;  // dimension pairs: one 128-bit shared load each
   const int d = D > 0 ? D : t.d;
-  __shared__ float2 s_q[kWarps][DM][32];
+  __shared__ float4 s_q[kWarps][32][DP];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const size_t n = t.n, total = t.total, m = q.m;
 
   unsigned long long base0 = 0;
   if (WRITE) {
+    if (records_complete(ra)) return;  // the replay kernel writes this range
     base0 = w.start[w.b_idx];
     const unsigned long long need = w.start[w.e_idx] - base0;
     if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -102,16 +109,27 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
         const float2 v = valid ? q.qe[k * m + pos] : make_float2(INFINITY, -INFINITY);
         ql[k] = v.x;
         qh[k] = v.y;
-        s_q[wib][k][lane] = v;
         gl[k] = warp_min(v.x);  // packet bounding box
         gh[k] = warp_max(v.y);
       }
+    }
+#pragma unroll
+    for (int k2 = 0; k2 < DP; ++k2) {
+      const int a = 2 * k2, b = 2 * k2 + 1;
+      if (a < d)
+        s_q[wib][lane][k2] = make_float4(ql[a], qh[a], b < d ? ql[b] : 0.f, b < d ? qh[b] : 0.f);
     }
     uint32_t cnt = 0;
     unsigned long long out = 0;
     if (WRITE && valid) out = w.start[w.by_pos ? pos : Q] - base0;
     __syncwarp();
 
+    // Records of the count pass: one per (query, leaf) with hits, written
+    // leaf by leaf with one coalesced store.  After the arena runs out the
+    // packet stops writing but keeps counting the blocks it would need.
+    const bool recording = !WRITE && ra.max_blocks > 0;
+    bool rec_write = recording;
+    uint32_t cur_blk = kNoBlock, fill = kRecBlock, nblk = 0;
     // Test the 32 level-1 nodes (leaves) from g1 on against the packet box,
     // then run the packet's queries over each surviving leaf.
     auto leaves = [&](uint32_t g1) {
@@ -152,15 +170,18 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
           if (k < d) ev[k] = iv ? t.e[k * n + i] : make_float2(INFINITY, -INFINITY);
         uint32_t my_sid = 0;
         if (WRITE && iv) my_sid = t.sid[i];
+        uint32_t my_hb = 0;  // count pass: this lane's query's hit mask in the leaf
         while (qm) {
           const int qq = __ffs(qm) - 1;
           qm &= qm - 1u;
           bool hit = iv;
 #pragma unroll
-          for (int k = 0; k < DM; ++k) {
-            if (k < d) {
-              const float2 b = s_q[wib][k][qq];
-              hit = hit & le<OPEN>(ev[k].x, b.y) & le<OPEN>(b.x, ev[k].y);
+          for (int k2 = 0; k2 < DP; ++k2) {
+            if (2 * k2 < d) {
+              const float4 b = s_q[wib][qq][k2];
+              hit = hit & le<OPEN>(ev[2 * k2].x, b.y) & le<OPEN>(b.x, ev[2 * k2].y);
+              if (2 * k2 + 1 < d)
+                hit = hit & le<OPEN>(ev[2 * k2 + 1].x, b.w) & le<OPEN>(b.z, ev[2 * k2 + 1].y);
             }
           }
           const uint32_t hb = __ballot_sync(0xffffffffu, hit);
@@ -178,9 +199,44 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
             }
             if (lane == qq) out = o + __popc(hb);
           } else {
-            if (lane == qq) cnt += __popc(hb);
+            if (lane == qq) my_hb = hb;
           }
         }
+        if (recording) {
+          const uint32_t rm = __ballot_sync(0xffffffffu, my_hb != 0u);
+          if (rm) {
+            const uint32_t k = __popc(rm);
+            if (fill + k > kRecBlock) {  // the leaf's records start a new block
+              ++nblk;
+              if (rec_write) {
+                uint32_t b = 0;
+                if (lane == 0) b = atomicAdd(&ra.blk_counter[0], 1u);
+                b = __shfl_sync(0xffffffffu, b, 0);
+                if (b >= ra.max_blocks) {
+                  rec_write = false;  // arena exhausted: the write pass walks instead
+                } else {
+                  if (lane == 0) {
+                    if (cur_blk == kNoBlock) {
+                      ra.pkt_first[p] = b;
+                    } else {
+                      ra.blk_next[cur_blk] = b;
+                      ra.blk_count[cur_blk] = fill;
+                    }
+                    ra.blk_pkt[b] = p;
+                  }
+                  ra.blk_base[(size_t)b * 32u + lane] = cnt;  // matches before this leaf
+                  cur_blk = b;
+                }
+              }
+              fill = 0;
+            }
+            if (rec_write && my_hb != 0u)
+              ra.rec[(size_t)cur_blk * kRecBlock + fill + __popc(rm & lt)] =
+                  make_uint2(((g1 + cl) << 5) | (uint32_t)lane, my_hb);
+            fill += k;
+          }
+        }
+        if (!WRITE) cnt += __popc(my_hb);
       }
     };
 
@@ -238,13 +294,120 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
       counts[Q] = cnt;
       if (counts_pos) counts_pos[pos] = cnt;
     }
+    if (recording && lane == 0) {
+      if (rec_write) {
+        if (cur_blk == kNoBlock) {
+          ra.pkt_first[p] = kNoBlock;
+        } else {
+          ra.blk_next[cur_blk] = kNoBlock;
+          ra.blk_count[cur_blk] = fill;
+        }
+      }
+      ra.pkt_nblk[p] = rec_write ? nblk : 0u;
+      if (nblk) atomicAdd(&ra.blk_counter[1], nblk);
+    }
+  }
+}
+
+// Plan-order list of record blocks: one thread per packet copies its chain.
+__global__ void k_block_list(RecordArena ra, uint32_t packets) {
+  if (!records_complete(ra)) return;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < packets;
+       p += gridDim.x * blockDim.x) {
+    unsigned long long at = ra.pkt_off[p];
+    for (uint32_t b = ra.pkt_first[p]; b != kNoBlock; b = ra.blk_next[b]) ra.blk_list[at++] = b;
+  }
+}
+
+// Write pass from the records of the count pass.  Work unit: one record
+// block (up to 512 records of one packet), taken from the plan-order block
+// list, so uneven packets spread over the whole GPU.  A warp loads the
+// block's packet queries, starts each query's cursor at its output offset
+// plus the matches it had before the block, and expands the records 32 at a
+// time (one coalesced load) in groups of 8: the subscription ids of the 8
+// records are loaded first (independent loads in flight together), then the
+// records are written in order.  For a record of query lane qq and leaf g
+// the lanes holding a set bit of the hit mask write (update, subscription)
+// pairs from qq's cursor, exactly as the walking write pass would have.
+// Cursors are relative to the range's first pair; with fewer than 2^32 pairs
+// in the range (WIDE false) they are 32-bit.
+template <bool FILTER_ID, bool WIDE>
+__global__ void __launch_bounds__(kThreads, 6)
+k_replay(TreeView t, QueryView q, RecordArena ra, WriteView w, uint32_t p0, uint32_t p1,
+         uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide, uint32_t* __restrict__ work,
+         Status* __restrict__ st) {
+  using Cursor = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+  const int lane = threadIdx.x & 31;
+  const uint32_t lt = lanemask_lt();
+  if (!records_complete(ra)) return;  // the walking write pass handles this range
+  const unsigned long long base0 = w.start[w.b_idx];
+  const unsigned long long need = w.start[w.e_idx] - base0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    st->K = need;
+    if (need > w.capacity) atomicOr(&st->err, kErrCapacity);
+  }
+  // Pair positions are bounded by construction: every cursor starts at its
+  // update's offset plus the matches before the block and advances by the
+  // popcounts that the count pass summed into that update's count, so all
+  // writes stay below need <= capacity.
+  if (need > w.capacity) return;
+  if (!WIDE && need > 0xffffffffull) return;  // host picks WIDE for such ranges
+  const unsigned long long i0 = ra.pkt_off[p0], i1 = ra.pkt_off[p1];
+  for (;;) {
+    unsigned long long i = 0;
+    if (lane == 0) i = i0 + atomicAdd(work, 1u);
+    i = __shfl_sync(0xffffffffu, i, 0);
+    if (i >= i1) break;
+    const uint32_t blk = ra.blk_list[i];
+    const uint32_t p = ra.blk_pkt[blk];
+    const uint32_t pos = p * 32u + lane;
+    bool valid = pos >= pb && pos < pe;
+    uint32_t Q = 0;
+    if (valid) Q = q.qid[pos];
+    if (FILTER_ID) valid = valid && Q >= idb && Q < ide;
+    Cursor out = 0;
+    if (valid)
+      out = (Cursor)(w.start[w.by_pos ? pos : Q] - base0) + (Cursor)ra.blk_base[(size_t)blk * 32u + lane];
+    const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    if (vmask == 0u) continue;
+    const bool all_valid = vmask == 0xffffffffu;
+    const uint32_t nrec = ra.blk_count[blk];
+    const uint2* rec = ra.rec + (size_t)blk * kRecBlock;
+    for (uint32_t r0 = 0; r0 < nrec; r0 += 32u) {
+      const uint2 mine = r0 + lane < nrec ? rec[r0 + lane] : make_uint2(0u, 0u);
+      const uint32_t cnt = min(32u, nrec - r0);
+      for (uint32_t j0 = 0; j0 < cnt; j0 += 8u) {
+        uint32_t xs[8], hs[8], ss[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          xs[u] = __shfl_sync(0xffffffffu, mine.x, j0 + u);
+          hs[u] = __shfl_sync(0xffffffffu, mine.y, j0 + u);  // 0 past the end
+          if (!all_valid && !((vmask >> (xs[u] & 31u)) & 1u)) hs[u] = 0u;
+          ss[u] = ((hs[u] >> lane) & 1u) ? t.sid[(xs[u] >> 5) * 32u + lane] : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          if (hs[u] == 0u) continue;
+          const int qq = (int)(xs[u] & 31u);
+          const Cursor o = __shfl_sync(0xffffffffu, out, qq);
+          const uint32_t Qq = __shfl_sync(0xffffffffu, Q, qq);
+          if ((hs[u] >> lane) & 1u) {
+            ddm_pair pr;
+            pr.upd = Qq;
+            pr.sub = ss[u];
+            w.pairs[(unsigned long long)(o + (Cursor)__popc(hs[u] & lt))] = pr;
+          }
+          if (lane == qq) out = o + (Cursor)__popc(hs[u]);
+        }
+      }
+    }
   }
 }
 
 template <bool WRITE>
 cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                           uint32_t* counts_pos, const WriteView& w, uint32_t* work, Status* st,
-                           int sms, cudaStream_t s) {
+                           uint32_t* counts_pos, const RecordArena& ra, const WriteView& w,
+                           uint32_t* work, Status* st, int sms, cudaStream_t s) {
   if (q.nq == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
@@ -254,7 +417,7 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags
   const uint32_t cap = (uint32_t)sms * 8u;
   if (blocks > cap) blocks = cap;
 #define DDM_LAUNCH(DD, OP) \
-  k_packets<DD, OP, WRITE><<<blocks, kThreads, 0, s>>>(t, q, counts, counts_pos, w, work, st)
+  k_packets<DD, OP, WRITE><<<blocks, kThreads, 0, s>>>(t, q, counts, counts_pos, ra, w, work, st)
   switch (t.d) {
     case 1: open ? DDM_LAUNCH(1, true) : DDM_LAUNCH(1, false); break;
     case 2: open ? DDM_LAUNCH(2, true) : DDM_LAUNCH(2, false); break;
@@ -269,14 +432,50 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags
 }  // namespace
 
 cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                         uint32_t* counts_pos, uint32_t* work, int sms, cudaStream_t s) {
+                         uint32_t* counts_pos, const RecordArena& ra, uint32_t* work, int sms,
+                         cudaStream_t s) {
   WriteView w{};
-  return launch_packets<false>(t, q, flags, counts, counts_pos, w, work, nullptr, sms, s);
+  return launch_packets<false>(t, q, flags, counts, counts_pos, ra, w, work, nullptr, sms, s);
 }
 
 cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, const WriteView& w,
-                         uint32_t* work, Status* st, int sms, cudaStream_t s) {
-  return launch_packets<true>(t, q, flags, nullptr, nullptr, w, work, st, sms, s);
+                         const RecordArena& ra, uint32_t* work, Status* st, int sms,
+                         cudaStream_t s) {
+  return launch_packets<true>(t, q, flags, nullptr, nullptr, ra, w, work, st, sms, s);
+}
+
+cudaError_t launch_block_list(const RecordArena& ra, uint32_t packets, cudaStream_t s) {
+  if (packets == 0 || ra.max_blocks == 0) return cudaSuccess;
+  uint32_t blocks = (packets + 255) / 256;
+  if (blocks > 4096) blocks = 4096;
+  k_block_list<<<blocks, 256, 0, s>>>(ra, packets);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_replay(const TreeView& t, const QueryView& q, const RecordArena& ra,
+                          const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
+                          bool id_filter, uint32_t idb, uint32_t ide, uint32_t* work, Status* st,
+                          int sms, cudaStream_t s) {
+  if (p1 <= p0) return cudaSuccess;
+  cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
+  if (e) return e;
+  const uint32_t blocks = (uint32_t)sms * 6u;  // persistent: work = record blocks
+  // Cursors fit 32 bits when the range's pairs do; the capacity bounds them.
+  const bool wide = w.capacity > 0xffffffffull;
+  if (id_filter) {
+    if (wide)
+      k_replay<true, true><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+    else
+      k_replay<true, false><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+  } else {
+    if (wide)
+      k_replay<false, true><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+    else
+      k_replay<false, false><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+  }
+  note_launches(1);
+  return cudaGetLastError();
 }
 
 }  // namespace ddm

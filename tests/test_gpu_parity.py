@@ -262,6 +262,46 @@ def test_ordered_chunks_cover_the_same_pairs(ctx):
     assert np.array_equal(got[sel, 1], ps[off[j]:off[j + 1]])
 
 
+def test_replay_and_walking_write_agree(ctx):
+    """The write pass expands the count pass's records when they fit the
+    record budget and walks the tree otherwise; both give the same list."""
+    import torch
+    arrays = W.clustered_lognormal(30000, 25000, d=3, alpha=100.0, seed=21)
+    U = to_dev(arrays)
+    results = []
+    fresh = ddm.ddm_create(0)
+    try:
+        for budget in (None, 0, 1 << 16):
+            if budget is not None:
+                ddm.ddm_set_replay_budget(fresh, budget)
+            for rep in range(2):     # the second plan uses the first one's size hint
+                K = ddm.ddm_count(fresh, *U)
+                pairs = torch.empty((K, 2), dtype=torch.int32, device="cuda")
+                assert ddm.ddm_match(fresh, *U, pairs) == K
+                full = pairs.cpu().numpy().view(np.uint32).copy()
+                ddm.ddm_build(fresh, U[2], U[3])
+                ddm.ddm_plan(fresh, U[0], U[1])
+                ooff = torch.empty(25001, dtype=torch.int64, device="cuda")
+                ddm.ddm_plan_order(fresh, None, ooff)
+                torch.cuda.synchronize()
+                ooff = ooff.cpu().numpy()
+                a, b = 777, 20001            # a range that starts and ends inside packets
+                part = torch.empty((int(ooff[b] - ooff[a]), 2), dtype=torch.int32, device="cuda")
+                assert ddm.ddm_write_ordered(fresh, a, b, part) == ooff[b] - ooff[a]
+                sub = torch.empty((K, 2), dtype=torch.int32, device="cuda")
+                ks = ddm.ddm_write(fresh, 3000, 9000, sub)
+                results.append((full, part.cpu().numpy().copy(), sub[:ks].cpu().numpy().copy()))
+    finally:
+        ddm.ddm_destroy(fresh)
+    for r in results[1:]:
+        for x, y in zip(results[0], r):
+            assert np.array_equal(x, y)
+    Ko, ou, os_ = oracle.itm_pairs(*arrays)
+    full = results[0][0]
+    assert np.array_equal(full[:, 0], ou)
+    assert np.array_equal(np.sort(keys(full[:, 0], full[:, 1])), np.sort(keys(ou, os_)))
+
+
 # --- error paths -------------------------------------------------------------
 
 def test_invalid_extents(ctx):
