@@ -37,6 +37,10 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
+# DRAM bytes (read + write) per pair of the write-pass kernel (k_replay), from
+# the ncu capture summarised in profiles/k_replay_clustered_d3_scale0.15.md
+# (a smaller case of the same workload; traffic scales with pairs written).
+TRAFFIC_PER_PAIR = 10.25
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -64,6 +68,20 @@ def dist():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def job_totals(t_local, pairs_local, world, device="cpu"):
+    """Whole-job timing over ranks: the slowest rank's time and the pairs of
+    all ranks (the only use of the process group; no data-path collective)."""
+    if world <= 1:
+        return t_local, float(pairs_local)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([t_local], dtype=torch.float64, device=device)
+    k = torch.tensor([float(pairs_local)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    tdist.all_reduce(k, op=tdist.ReduceOp.SUM)
+    return float(t[0]), float(k[0])
 
 
 def workload(name, rank, scale=1.0):
@@ -217,12 +235,18 @@ def main():
     pairs = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    write_ms, write_bytes = [], []
+    write_ms, write_bytes, write_pairs, plan_ms = [], [], [], []
     chunks = [0]
 
     def step(record=False):
+        if record:
+            a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
         ddm.ddm_build(ctx, dev[2], dev[3])
         K = ddm.ddm_plan(ctx, dev[0], dev[1])
+        if record:
+            a1.record(stream)
+            plan_ms.append((a0, a1))
         b = 0
         chunks[0] = 0
         while b < m:
@@ -236,6 +260,7 @@ def main():
                 s1.record(stream)
                 write_ms.append((s0, s1))
                 write_bytes.append(8 * d * (e - b) + 8 * d * n + 8 * k)
+                write_pairs.append(k)
             b = e
         return K
 
@@ -259,14 +284,7 @@ def main():
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     t_local = total_ms / 1e3
     pairs_local = K * args.steps
-    if world > 1:
-        tt = torch.tensor([t_local, float(pairs_local)], dtype=torch.float64, device="cuda")
-        mx = tt.clone()
-        tdist.all_reduce(mx[0:1], op=tdist.ReduceOp.MAX)
-        tdist.all_reduce(tt[1:2], op=tdist.ReduceOp.SUM)
-        t_job, pairs_job = float(mx[0]), float(tt[1])
-    else:
-        t_job, pairs_job = t_local, float(pairs_local)
+    t_job, pairs_job = job_totals(t_local, pairs_local, world, device="cuda")
     wtimes = [a.elapsed_time(b) for a, b in write_ms]
     write_s = sum(wtimes) / 1e3
     write_gbs = sum(write_bytes) / write_s / 1e9 if write_s > 0 else 0.0
@@ -352,10 +370,17 @@ def main():
         "p99_ms": float(np.percentile(step_ms, 99)),
         "roofline": {"bound": "hbm", "kernel": "k_packets<write> (ddm_write_ordered)",
                      "achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": write_gbs / hbm_peak, "traffic": None,
+                     "frac": write_gbs / hbm_peak,
+                     "traffic": TRAFFIC_PER_PAIR * sum(write_pairs) / max(1, len(write_pairs)),
+                     "traffic_note": "bytes per launch, scaled from an ncu capture of a smaller "
+                                     "case by pairs written (see DESIGN.md, profiles/)",
                      "peak_source": peak_src,
                      "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 8*(pairs in chunk)",
                      "write_ms_per_step": 1e3 * write_s / args.steps},
+        "phases_ms_per_step": {
+            "build_and_count": sum(a.elapsed_time(b) for a, b in plan_ms) / args.steps,
+            "write": 1e3 * write_s / args.steps,
+            "count_bound": "alu (issue-bound tree walk, see profiles/)"},
         "e2e": e2e,
         "gpu_launches": int(launches),
         "cpu_baseline": cpu,
