@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=15.0, help="oracle sample budget")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true",
+                    help="skip the batched-instances comparison (4,096 problems)")
+    ap.add_argument("--batched-only", action="store_true",
+                    help="run only the batched-instances comparison")
     return ap.parse_args()
 
 
@@ -186,6 +190,90 @@ def cpu_oracle_sample(arrays, budget_s):
             "queries_per_s": m / t_all, "seconds": wall}
 
 
+def batched_section(reps: int = 3):
+    """Batched instances: 4,096 independent d = 2 problems with log-uniform
+    sizes in [100, 1e5] extents (alpha = 1 each).  Plain: one ddm_match per
+    instance (each with its own host synchronisation).  Batched: the
+    autotuned ddm_batch_match_async recorded once into a CUDA graph and
+    replayed.  Both produce the same pairs (checked by count)."""
+    import numpy as np
+    import torch
+
+    import paper_1309_3458_gb300 as ddm
+    from paper_1309_3458_gb300 import autotune as AT
+    from paper_1309_3458_gb300 import workloads as W
+    inst = W.batched_instances(4096, d=2, alpha=1.0, size_lo=100, size_hi=100_000, seed=0)
+    ulo, uhi, uoff, slo, shi, soff = W.concat_instances(inst)
+    ctx = ddm.ddm_create(torch.cuda.current_device())
+    try:
+        # plain per-instance calls
+        per = [tuple(torch.from_numpy(a).cuda() for a in x) for x in inst]
+        Ks = [ddm.ddm_count(ctx, *u) for u in per]
+        K = int(sum(Ks))
+        buf = torch.empty((K + 1, 2), dtype=torch.int32, device="cuda")
+        stream = torch.cuda.current_stream()
+
+        def plain():
+            o = 0
+            for u, k in zip(per, Ks):
+                ddm.ddm_match(ctx, *u, buf[o:])
+                o += k
+
+        plain()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            plain()
+        ev[1].record(stream)
+        torch.cuda.synchronize()
+        plain_ms = ev[0].elapsed_time(ev[1]) / reps
+
+        # batched
+        U = tuple(torch.from_numpy(a).cuda() for a in (ulo, uhi, slo, shi))
+        uo = torch.from_numpy(uoff.astype(np.int64)).cuda()
+        so = torch.from_numpy(soff.astype(np.int64)).cuda()
+        pof = torch.empty(len(inst) + 1, dtype=torch.int64, device="cuda")
+        kd = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ed = torch.zeros(1, dtype=torch.int32, device="cuda")
+        s = torch.cuda.Stream()
+        s.wait_stream(stream)
+
+        def batched():
+            ddm.ddm_batch_match_async(ctx, U[0], U[1], uo, U[2], U[3], so, buf, pof, kd, ed,
+                                      stream=s)
+
+        with torch.cuda.stream(s):
+            best, table = AT.autotune(ctx, batched, stream=s)
+            batched()
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            batched()
+        kd.zero_()
+        torch.cuda.synchronize()
+        with torch.cuda.stream(s):   # replay() launches on the current stream
+            g.replay()
+        torch.cuda.synchronize()
+        Kb, err = int(kd[0]), int(ed[0])
+        ev2 = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        with torch.cuda.stream(s):
+            ev2[0].record(s)
+            for _ in range(reps * 4):
+                g.replay()
+            ev2[1].record(s)
+        torch.cuda.synchronize()
+        batched_ms = ev2[0].elapsed_time(ev2[1]) / (reps * 4)
+        return {"workload": "4096 instances, d=2, alpha=1, sizes log-uniform [100, 1e5]",
+                "extents": int(uoff[-1] + soff[-1]), "K": K, "K_batched": Kb, "err": err,
+                "plain_ms": plain_ms, "batched_ms": batched_ms,
+                "plain_pairs_per_s": K / plain_ms * 1e3,
+                "batched_pairs_per_s": Kb / batched_ms * 1e3,
+                "speedup": plain_ms / batched_ms, "tuning": best,
+                "tuning_table_ms": [[round(t, 3), c] for t, c in table]}
+    finally:
+        ddm.ddm_destroy(ctx)
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -219,6 +307,9 @@ def main():
 
     import paper_1309_3458_gb300 as ddm
     torch.cuda.set_device(local)
+    if args.batched_only:
+        print(json.dumps({"batched": batched_section()}), flush=True)
+        return
     if world > 1:
         tdist.init_process_group("nccl")
 
@@ -341,6 +432,12 @@ def main():
     if rank != 0:
         return
 
+    batched = None
+    if not args.no_batched and world == 1:
+        del pairs
+        torch.cuda.empty_cache()
+        batched = batched_section()
+
     cpu = None
     if not args.no_cpu and world == 1:
         cpu = cpu_oracle_sample(arrays, args.cpu_seconds)
@@ -385,6 +482,7 @@ def main():
         "gpu_launches": int(launches),
         "cpu_baseline": cpu,
         "clocks": clocks,
+        "batched": batched,
     }
     print(json.dumps(line), flush=True)
 

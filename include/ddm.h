@@ -194,6 +194,53 @@ int ddm_chunk_end_ordered(ddm_ctx *ctx, uint32_t pos_begin, uint64_t capacity,
                           uint32_t *pos_end, void *stream);
 
 /* ---------------------------------------------------------------------- */
+/* Batched instances                                                       */
+/* ---------------------------------------------------------------------- */
+
+/* Match `count` independent problems in one call (the per-update queries of
+ * every instance are independent, Section IV "Parallelizing ITM", so all
+ * instances share one sort, one tree build, one counting launch and one
+ * write launch).  Instance i's updates are positions
+ * [upd_off[i], upd_off[i+1]) of one SoA update array of m_total extents
+ * (row k at k*m_total); its subscriptions are positions
+ * [sub_off[i], sub_off[i+1]) of one SoA subscription array of n_total
+ * extents.  upd_off / sub_off: DEVICE arrays of count + 1 nondecreasing
+ * uint64 with upd_off[0] = sub_off[0] = 0, upd_off[count] = m_total,
+ * sub_off[count] = n_total (not checked; empty instances are allowed).
+ * An update only matches subscriptions of its own instance.  Pairs carry
+ * instance-local ids (update j of instance i is upd_off[i] + j of the
+ * array); they are grouped by instance, then by update.  pair_off
+ * (optional, DEVICE, count + 1 uint64) receives each instance's first pair;
+ * pair_off[count] = K.  *k_out = K.  DDM_ERR_CAPACITY when K > capacity
+ * (nothing written).  Synchronises `stream` once.  Errors: DDM_ERR_ARG
+ * (count 0, NULL offsets, ...), DDM_ERR_EXTENT, DDM_ERR_CAPACITY,
+ * DDM_ERR_NOMEM, DDM_ERR_CUDA, DDM_ERR_TIMEOUT.  Afterwards the staged
+ * single-problem calls report DDM_ERR_STATE until the next ddm_build. */
+int ddm_batch_match(ddm_ctx *ctx, int d, uint32_t count,
+                    const float *upd_lo, const float *upd_hi, const uint64_t *upd_off,
+                    uint32_t m_total,
+                    const float *sub_lo, const float *sub_hi, const uint64_t *sub_off,
+                    uint32_t n_total,
+                    uint32_t flags, ddm_pair *pairs, uint64_t capacity, uint64_t *pair_off,
+                    uint64_t *k_out, void *stream);
+
+/* As ddm_batch_match without any host synchronisation, so that the call can
+ * be recorded into a CUDA graph: K goes to k_dev[0] and the device error
+ * bits to err_dev[0] (1 = invalid extent, 2 = bounded wait timed out,
+ * 4 = more pairs than capacity, nothing written), both DEVICE pointers
+ * (either may be NULL).  The call allocates device memory when its sizes
+ * grow, which a captured stream does not allow: make one ddm_batch_match
+ * (or ddm_batch_match_async) call with the same sizes before capturing.
+ * Returns DDM_OK once the work is enqueued. */
+int ddm_batch_match_async(ddm_ctx *ctx, int d, uint32_t count,
+                          const float *upd_lo, const float *upd_hi, const uint64_t *upd_off,
+                          uint32_t m_total,
+                          const float *sub_lo, const float *sub_hi, const uint64_t *sub_off,
+                          uint32_t n_total,
+                          uint32_t flags, ddm_pair *pairs, uint64_t capacity, uint64_t *pair_off,
+                          uint64_t *k_dev, uint32_t *err_dev, void *stream);
+
+/* ---------------------------------------------------------------------- */
 /* Introspection of the built tree (for checking intermediate results)     */
 /* ---------------------------------------------------------------------- */
 
@@ -226,6 +273,17 @@ int ddm_tree_export(ddm_ctx *ctx, uint32_t *order, float *node_lo, float *node_h
  * run out of room and fall back to walking.  Results are identical either
  * way.  0 turns recording off.  DDM_ERR_ARG for a NULL context. */
 int ddm_set_replay_budget(ddm_ctx *ctx, uint64_t bytes);
+
+/* Tuning knobs (results never depend on them), picked per workload by the
+ * autotuner in the Python package:
+ *  str_shift   -- added to every re-sort group exponent of the tree order
+ *                 (-4..4; 0 = sort-tile-recursive sizes);
+ *  ctas_per_sm -- 256-thread CTAs per SM of the query kernels (1..32,
+ *                 default 8; the kernels are persistent);
+ *  replay      -- nonzero: the write pass may replay the count pass's
+ *                 records; 0: it walks the tree again.
+ * DDM_ERR_ARG outside these ranges. */
+int ddm_set_tuning(ddm_ctx *ctx, int str_shift, uint32_t ctas_per_sm, uint32_t replay);
 
 /* Testing aid: make device workspace allocations that would bring the
  * context's total above `bytes` fail with DDM_ERR_NOMEM (0 = no limit). */

@@ -60,8 +60,13 @@ SIGNATURES = {
     "ddm_tree_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "ddm_debug_set_alloc_limit": (_i, [_vp, _u64]),
     "ddm_set_replay_budget": (_i, [_vp, _u64]),
+    "ddm_set_tuning": (_i, [_vp, _i, _u32, _u32]),
     "ddm_debug_launch_count": (_u64, []),
     "ddm_scan_counts_noalloc": (_i, [_vp, _u32, _vp, _vp]),
+    "ddm_batch_match": (_i, [_vp, _i, _u32, _vp, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _u32, _vp,
+                             _u64, _vp, _pu64, _vp]),
+    "ddm_batch_match_async": (_i, [_vp, _i, _u32, _vp, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _u32,
+                                   _vp, _u64, _vp, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -236,6 +241,10 @@ def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=Non
                                  _stream(stream)), "ddm_tree_export")
 
 
+def ddm_set_tuning(ctx: int, str_shift: int = 0, ctas_per_sm: int = 8, replay: int = 1) -> None:
+    _check(lib().ddm_set_tuning(ctx, str_shift, ctas_per_sm, replay), "ddm_set_tuning")
+
+
 def ddm_set_replay_budget(ctx: int, nbytes: int) -> None:
     _check(lib().ddm_set_replay_budget(ctx, nbytes), "ddm_set_replay_budget")
 
@@ -253,3 +262,35 @@ def ddm_scan_counts_noalloc(counts, offsets, stream=None) -> None:
     device tensor, m) without any allocation; see include/ddm.h."""
     _check(lib().ddm_scan_counts_noalloc(_ptr(counts), counts.shape[0], _ptr(offsets),
                                          _stream(stream)), "ddm_scan_counts_noalloc")
+
+
+def ddm_batch_match(ctx: int, upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub_off, pairs,
+                    pair_off=None, flags: int = DDM_CLOSED, stream=None) -> int:
+    """Batched instances (see include/ddm.h).  upd_off / sub_off: int64 device
+    tensors of count + 1 offsets; pairs: int32 device tensor (capacity, 2)."""
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d2, sl, sh, n = _set(sub_lo, sub_hi)
+    assert d == d2
+    count = upd_off.shape[0] - 1
+    cap = 0 if pairs is None else pairs.shape[0]
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_batch_match(ctx, d, count, ul, uh, _ptr(upd_off), m, sl, sh, _ptr(sub_off), n,
+                               flags, _ptr(pairs), cap, _ptr(pair_off), ctypes.byref(k),
+                               _stream(stream))
+    _check(rc, "ddm_batch_match", k.value)
+    return k.value
+
+
+def ddm_batch_match_async(ctx: int, upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub_off, pairs,
+                          pair_off=None, k_dev=None, err_dev=None, flags: int = DDM_CLOSED,
+                          stream=None) -> None:
+    """Host-synchronisation-free batched match (capturable in a CUDA graph)."""
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d2, sl, sh, n = _set(sub_lo, sub_hi)
+    assert d == d2
+    count = upd_off.shape[0] - 1
+    cap = 0 if pairs is None else pairs.shape[0]
+    rc = lib().ddm_batch_match_async(ctx, d, count, ul, uh, _ptr(upd_off), m, sl, sh,
+                                     _ptr(sub_off), n, flags, _ptr(pairs), cap, _ptr(pair_off),
+                                     _ptr(k_dev), _ptr(err_dev), _stream(stream))
+    _check(rc, "ddm_batch_match_async")

@@ -48,6 +48,13 @@ struct ddm_ctx {
   uint32_t rec_blocks = 0;      // blocks of the current arena
   uint32_t rec_hint = 0;        // blocks the last count pass asked for
   RecordArena arena{};          // arena of the current plan (max_blocks 0 = none)
+  // batched instances
+  DevBuf inst_s, inst_u, bglog2, bngroups, bgbase;
+  BatchView bv{};               // count 0 = single problem
+  // tuning knobs (ddm_set_tuning)
+  int str_shift = 0;            // added to the re-sort group exponents
+  uint32_t ctas_per_sm = 8;     // CTAs per SM of the packet kernels
+  bool replay_on = true;        // record / replay write pass allowed
 
   bool built = false;
   TreeView tree{};
@@ -171,6 +178,51 @@ int sort_pass(ddm_ctx* c, uint32_t cnt, int passes, int* cur, cudaStream_t s) {
 // then, for each further dimension with a group size, a stable re-sort by
 // that dimension's lower bound inside aligned groups.  Validates the set on
 // the way.  Returns the buffer pair whose vals hold the order.
+// Bytes needed to hold values 0..v.
+int key_bytes(uint64_t v) {
+  int b = 0;
+  while (v) {
+    ++b;
+    v >>= 8;
+  }
+  return b;
+}
+
+// Batched sets: the instance is the major sort key, and each instance's
+// re-sort groups are sized from its own extent count.
+struct BatchSet {
+  const unsigned long long* off;  // [count + 1] positions of each instance
+  uint32_t count;
+  uint32_t* inst;                 // [cnt] instance of each position (filled here)
+};
+
+int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
+                    const BatchSet& bs, int* cur, cudaStream_t s) {
+  *cur = 0;
+  DDM_TRY(ensure_sort(c, cnt));
+  DDM_TRY(ensure(c, c->bglog2, sizeof(int) * (bs.count ? bs.count : 1)));
+  DDM_TRY(ensure(c, c->bngroups, sizeof(uint32_t) * (bs.count ? bs.count : 1)));
+  DDM_TRY(ensure(c, c->bgbase, sizeof(unsigned long long) * ((size_t)bs.count + 1)));
+  DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * ((size_t)cnt / kScanTile + (size_t)bs.count / kScanTile + 2)));
+  DDM_CUDA(launch_fill_inst(bs.off, bs.count, bs.inst, s));
+  DDM_CUDA(launch_validate_batch(d, lo, hi, cnt, bs.inst,
+                                 static_cast<unsigned long long*>(c->keys[0].p),
+                                 static_cast<uint32_t*>(c->vals[0].p), c->st_dev, c->sms, s));
+  DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(bs.count ? bs.count - 1 : 0), cur, s));
+  for (int k = 1; k < d; ++k) {
+    auto* gl = static_cast<int*>(c->bglog2.p);
+    auto* ng = static_cast<uint32_t*>(c->bngroups.p);
+    auto* gb = static_cast<unsigned long long*>(c->bgbase.p);
+    DDM_CUDA(launch_batch_groups(bs.off, bs.count, d, k, c->str_shift, gl, ng, s));
+    DDM_CUDA(launch_scan(ng, bs.count, gb, static_cast<unsigned long long*>(c->sums.p), nullptr, s));
+    DDM_CUDA(launch_rekey_batch(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt,
+                                cnt, bs.inst, bs.off, gl, gb,
+                                static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
+    DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(cnt), cur, s));  // at most cnt groups
+  }
+  return DDM_OK;
+}
+
 int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt, bool tree,
               int* cur, cudaStream_t s) {
   *cur = 0;
@@ -180,7 +232,7 @@ int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
                            s));
   DDM_TRY(sort_pass(c, cnt, tree ? 8 : 4, cur, s));
   int glog2[DDM_MAX_DIMS];
-  str_groups(cnt, d, glog2);
+  str_groups(cnt, d, glog2, c->str_shift);
   for (int k = 1; k < d; ++k) {
     if (!glog2[k]) continue;
     DDM_CUDA(launch_rekey(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt, cnt,
@@ -194,8 +246,10 @@ int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
 
 // Validate S, sort it into tree order and build the tree (steps run on `s`,
 // no host synchronisation).
-int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n, cudaStream_t s) {
+int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n, cudaStream_t s,
+                const BatchSet* bs = nullptr) {
   c->built = false;
+  if (!bs) c->bv = BatchView{};
   c->planned = false;
   TreeView t{};
   t.d = d;
@@ -210,7 +264,10 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
   DDM_TRY(ensure(c, c->sid, sizeof(uint32_t) * n));
   DDM_TRY(ensure(c, c->nodes, sizeof(float2) * (size_t)d * t.total));
   int cur = 0;
-  DDM_TRY(order_set(c, d, slo, shi, n, true, &cur, s));
+  if (bs)
+    DDM_TRY(order_set_batch(c, d, slo, shi, n, *bs, &cur, s));
+  else
+    DDM_TRY(order_set(c, d, slo, shi, n, true, &cur, s));
   t.e = static_cast<const float2*>(c->e.p);
   t.sid = static_cast<const uint32_t*>(c->sid.p);
   t.nodes = static_cast<const float2*>(c->nodes.p);
@@ -220,6 +277,12 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
   c->tree = t;
   c->built = true;
   return DDM_OK;
+}
+
+// Grid size argument of the packet kernels (they launch 8 CTAs per "SM").
+int packet_sms(const ddm_ctx* c) {
+  const int v = (int)((uint64_t)c->sms * c->ctas_per_sm / 8u);
+  return v > 0 ? v : 1;
 }
 
 QueryView query_view(ddm_ctx* c) {
@@ -235,7 +298,7 @@ QueryView query_view(ddm_ctx* c) {
 
 // Validate U, sort it, count per update, scan (no host synchronisation).
 int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_t flags,
-               bool record, cudaStream_t s) {
+               bool record, cudaStream_t s, const BatchSet* bs = nullptr) {
   c->planned = false;
   const int d = c->tree.d;
   DDM_TRY(ensure(c, c->counts, sizeof(uint32_t) * (m ? m : 1)));
@@ -252,7 +315,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   auto* pos_offsets = static_cast<unsigned long long*>(c->pos_offsets.p);
   c->m = m;
   c->arena = RecordArena{};
-  if (record && m > 0 && c->tree.n > 0 && c->replay_budget > 0) {
+  if (record && c->replay_on && m > 0 && c->tree.n > 0 && c->replay_budget > 0) {
     const uint32_t packets = (m + 31) / 32;
     // bytes per block: records, next/count/packet/list entries, 32 base counts
     const uint64_t per_block = (uint64_t)kRecBlock * sizeof(uint2) + 36 * sizeof(uint32_t);
@@ -286,13 +349,16 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   }
   if (m > 0) {
     int cur = 0;
-    DDM_TRY(order_set(c, d, ulo, uhi, m, false, &cur, s));
+    if (bs)
+      DDM_TRY(order_set_batch(c, d, ulo, uhi, m, *bs, &cur, s));
+    else
+      DDM_TRY(order_set(c, d, ulo, uhi, m, false, &cur, s));
     DDM_CUDA(launch_gather(d, static_cast<const uint32_t*>(c->vals[cur].p), ulo, uhi, m,
                            static_cast<float2*>(c->qe.p), static_cast<uint32_t*>(c->qid.p), c->sms,
                            s));
     if (c->tree.n > 0) {
-      DDM_CUDA(launch_count(c->tree, query_view(c), flags, counts, counts_pos, c->arena,
-                            static_cast<uint32_t*>(c->work.p), c->sms, s));
+      DDM_CUDA(launch_count(c->tree, query_view(c), c->bv, flags, counts, counts_pos, c->arena,
+                            static_cast<uint32_t*>(c->work.p), packet_sms(c), s));
     } else {
       DDM_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * m, s));
       DDM_CUDA(cudaMemsetAsync(counts_pos, 0, sizeof(uint32_t) * m, s));
@@ -341,10 +407,10 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
     auto* work = static_cast<uint32_t*>(c->work.p);
     if (c->arena.max_blocks) {
       const bool full = begin == 0 && end == c->m;
-      DDM_CUDA(launch_replay(c->tree, query_view(c), c->arena, w, 0, (c->m + 31) / 32, 0, c->m,
+      DDM_CUDA(launch_replay(c->tree, query_view(c), c->bv, c->arena, w, 0, (c->m + 31) / 32, 0, c->m,
                              !full, begin, end, work, c->st_dev, c->sms, s));
     }
-    DDM_CUDA(launch_write(c->tree, q, c->flags, w, c->arena, work, c->st_dev, c->sms, s));
+    DDM_CUDA(launch_write(c->tree, q, c->bv, c->flags, w, c->arena, work, c->st_dev, packet_sms(c), s));
   } else {
     DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
   }
@@ -367,9 +433,9 @@ int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, u
     w.capacity = capacity;
     auto* work = static_cast<uint32_t*>(c->work.p);
     if (c->arena.max_blocks)
-      DDM_CUDA(launch_replay(c->tree, q, c->arena, w, pb / 32, (pe + 31) / 32, pb, pe, false, 0, 0,
+      DDM_CUDA(launch_replay(c->tree, q, c->bv, c->arena, w, pb / 32, (pe + 31) / 32, pb, pe, false, 0, 0,
                              work, c->st_dev, c->sms, s));
-    DDM_CUDA(launch_write(c->tree, q, c->flags, w, c->arena, work, c->st_dev, c->sms, s));
+    DDM_CUDA(launch_write(c->tree, q, c->bv, c->flags, w, c->arena, work, c->st_dev, packet_sms(c), s));
   } else {
     DDM_CUDA(cudaMemsetAsync(&c->st_dev->K, 0, sizeof(unsigned long long), s));
   }
@@ -437,7 +503,8 @@ int ddm_destroy(ddm_ctx* c) {
                     &c->counts_pos, &c->offsets, &c->pos_offsets, &c->sums, &c->work,
                     &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
                     &c->blk_pkt, &c->blk_base, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
-                    &c->blk_list, &c->blk_counter})
+                    &c->blk_list, &c->blk_counter, &c->inst_s, &c->inst_u, &c->bglog2,
+                    &c->bngroups, &c->bgbase})
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -449,6 +516,15 @@ int ddm_set_replay_budget(ddm_ctx* c, uint64_t bytes) {
   if (!c) return DDM_ERR_ARG;
   c->replay_budget = bytes;
   c->rec_hint = 0;
+  return DDM_OK;
+}
+
+int ddm_set_tuning(ddm_ctx* c, int str_shift, uint32_t ctas_per_sm, uint32_t replay) {
+  if (!c || str_shift < -4 || str_shift > 4 || ctas_per_sm < 1 || ctas_per_sm > 32)
+    return DDM_ERR_ARG;
+  c->str_shift = str_shift;
+  c->ctas_per_sm = ctas_per_sm;
+  c->replay_on = replay != 0;
   return DDM_OK;
 }
 
@@ -616,6 +692,71 @@ int ddm_match_range(ddm_ctx* c, int d, const float* ulo, const float* uhi, uint3
                     void* stream) {
   return match_impl(c, d, ulo, uhi, m, slo, shi, n, begin, end, flags, pairs, capacity, k_out,
                     stream, true);
+}
+
+static int batch_impl(ddm_ctx* c, int d, uint32_t count, const float* ulo, const float* uhi,
+                      const uint64_t* upd_off, uint32_t m, const float* slo, const float* shi,
+                      const uint64_t* sub_off, uint32_t n, uint32_t flags, ddm_pair* pairs,
+                      uint64_t capacity, uint64_t* pair_off, uint64_t* k_out, uint64_t* k_dev,
+                      uint32_t* err_dev, void* stream, bool sync) {
+  if (!c || d < 1 || d > DDM_MAX_DIMS || count == 0 || !upd_off || !sub_off || !set_ok(d, ulo, uhi, m) ||
+      !set_ok(d, slo, shi, n) || (flags & ~DDM_OPEN) || (!pairs && capacity > 0))
+    return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(ensure(c, c->inst_s, sizeof(uint32_t) * (n ? n : 1)));
+  DDM_TRY(ensure(c, c->inst_u, sizeof(uint32_t) * (m ? m : 1)));
+  DDM_TRY(reset_status(c, s));
+  const auto* uoff = reinterpret_cast<const unsigned long long*>(upd_off);
+  const auto* soff = reinterpret_cast<const unsigned long long*>(sub_off);
+  BatchSet bs_s{soff, count, static_cast<uint32_t*>(c->inst_s.p)};
+  BatchSet bs_u{uoff, count, static_cast<uint32_t*>(c->inst_u.p)};
+  DDM_TRY(build_async(c, d, slo, shi, n, s, &bs_s));
+  c->bv.count = count;
+  c->bv.upd_off = uoff;
+  c->bv.sub_off = soff;
+  c->bv.q_inst = static_cast<const uint32_t*>(c->inst_u.p);
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags, true, s, &bs_u));
+  DDM_TRY(write_async(c, 0, m, pairs, capacity, s));
+  if (pair_off && m > 0)
+    DDM_CUDA(launch_gather_offsets(static_cast<const unsigned long long*>(c->offsets.p), uoff,
+                                   count, reinterpret_cast<unsigned long long*>(pair_off), s));
+  else if (pair_off)
+    DDM_CUDA(cudaMemsetAsync(pair_off, 0, sizeof(uint64_t) * ((size_t)count + 1), s));
+  if (c->arena.max_blocks)
+    DDM_CUDA(cudaMemcpyAsync(&c->st_dev->aux, static_cast<uint32_t*>(c->blk_counter.p) + 1,
+                             sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  if (k_dev)
+    DDM_CUDA(cudaMemcpyAsync(k_dev, &c->st_dev->K, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  if (err_dev)
+    DDM_CUDA(cudaMemcpyAsync(err_dev, &c->st_dev->err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  // The tree and plan hold a batch: the single-problem staged calls must not use them.
+  c->built = c->planned = false;
+  if (!sync) return DDM_OK;
+  DDM_TRY(sync_status(c, s));
+  if (c->arena.max_blocks) c->rec_hint = (uint32_t)c->st_host->aux;
+  if (k_out) *k_out = c->st_host->K;
+  return status_code(*c->st_host);
+}
+
+int ddm_batch_match(ddm_ctx* c, int d, uint32_t count, const float* upd_lo, const float* upd_hi,
+                    const uint64_t* upd_off, uint32_t m_total, const float* sub_lo,
+                    const float* sub_hi, const uint64_t* sub_off, uint32_t n_total, uint32_t flags,
+                    ddm_pair* pairs, uint64_t capacity, uint64_t* pair_off, uint64_t* k_out,
+                    void* stream) {
+  return batch_impl(c, d, count, upd_lo, upd_hi, upd_off, m_total, sub_lo, sub_hi, sub_off,
+                    n_total, flags, pairs, capacity, pair_off, k_out, nullptr, nullptr, stream, true);
+}
+
+int ddm_batch_match_async(ddm_ctx* c, int d, uint32_t count, const float* upd_lo,
+                          const float* upd_hi, const uint64_t* upd_off, uint32_t m_total,
+                          const float* sub_lo, const float* sub_hi, const uint64_t* sub_off,
+                          uint32_t n_total, uint32_t flags, ddm_pair* pairs, uint64_t capacity,
+                          uint64_t* pair_off, uint64_t* k_dev, uint32_t* err_dev, void* stream) {
+  return batch_impl(c, d, count, upd_lo, upd_hi, upd_off, m_total, sub_lo, sub_hi, sub_off,
+                    n_total, flags, pairs, capacity, pair_off, nullptr, k_dev, err_dev, stream,
+                    false);
 }
 
 int ddm_tree_shape(ddm_ctx* c, int* levels, uint32_t* counts, uint32_t* total) {

@@ -1,6 +1,7 @@
 // Internal declarations shared by the libddm translation units.
 #pragma once
 
+#include <cmath>
 #include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -66,6 +67,32 @@ struct WriteView {
   unsigned long long capacity;
 };
 
+// Batched instances: instance i owns update positions [upd_off[i],
+// upd_off[i+1]) and subscription positions [sub_off[i], sub_off[i+1]) of the
+// concatenated sets; sorting keeps these ranges (the instance is the major
+// key), so they hold in sorted order too.  q_inst[p] = instance of the update
+// at sorted position p.  count == 0: a single problem.
+struct BatchView {
+  uint32_t count;
+  const unsigned long long* upd_off;  // [count + 1]
+  const unsigned long long* sub_off;  // [count + 1]
+  const uint32_t* q_inst;             // [m]
+};
+
+// Exponent of the sort-tile-recursive group size for re-sorting dimension k
+// (1 <= k < d) of a set of n extents: with nb = n/32 leaves each dimension
+// gets about nb^(1/d) slabs, so dimension k is re-sorted inside groups of
+// 32 * nb^((d-k)/d) positions, rounded to a power of two.  0 = no re-sort
+// (groups of fewer than 64 would not change any leaf's box).
+__host__ __device__ inline int str_group_log2(uint32_t n, int d, int k, int shift = 0) {
+  if (n < 64u) return 0;
+  const double nb = (double)((n + 31u) / 32u);
+  const double G = 32.0 * pow(nb, (double)(d - k) / (double)d);
+  const int g = (int)floor(log2(G) + 0.5) + shift;
+  if (g < 6 || (1ull << g) >= (unsigned long long)n) return 0;
+  return g;
+}
+
 // Order-preserving map from float to uint32 (IEEE order; -0 maps like +0).
 __host__ __device__ inline uint32_t float_key(float f) {
 #ifdef __CUDA_ARCH__
@@ -92,6 +119,22 @@ cudaError_t launch_validate(int d, const float* lo, const float* hi, uint32_t cn
 // keys[i] = (i >> glog2) << 32 | key(lo_k[vals[i]]): re-sort inside groups.
 cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, int glog2,
                          unsigned long long* keys, int sms, cudaStream_t s);
+// Batched sets: inst[i] = instance owning position i (off has count+1 entries).
+cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t* inst,
+                             cudaStream_t s);
+// Batched validation + keys: keys[i] = inst[i] << 32 | key(lo0[i]).
+cudaError_t launch_validate_batch(int d, const float* lo, const float* hi, uint32_t cnt,
+                                  const uint32_t* inst, unsigned long long* keys, uint32_t* vals,
+                                  Status* st, int sms, cudaStream_t s);
+// Per instance and dimension k >= 1: group exponent (0 = groups of 1) and
+// group count, for the batched re-sorts.  glog2/ngroups: [count] each.
+cudaError_t launch_batch_groups(const unsigned long long* off, uint32_t count, int d, int k,
+                                int shift, int* glog2, uint32_t* ngroups, cudaStream_t s);
+// Batched re-sort keys: group = gbase[inst] + (local position >> glog2[inst]).
+cudaError_t launch_rekey_batch(const uint32_t* vals, const float* lo_k, uint32_t cnt,
+                               const uint32_t* inst, const unsigned long long* off,
+                               const int* glog2, const unsigned long long* gbase,
+                               unsigned long long* keys, int sms, cudaStream_t s);
 // qe[k][i] = (lo_k, hi_k)[vals[i]], qid[i] = vals[i].
 cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const float* hi,
                           uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s);
@@ -115,8 +158,9 @@ cudaError_t launch_sort64(SortScratch sc, uint32_t n, int passes, int* out_buf, 
 // ---- ddm_tree.cu ----------------------------------------------------------
 void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* total);
 // Group sizes (log2) of the per-dimension re-sorts: dimension k >= 1 is
-// re-sorted by lower bound inside aligned groups of 2^glog2[k] positions.
-void str_groups(uint32_t n, int d, int* glog2);
+// re-sorted by lower bound inside aligned groups of 2^glog2[k] positions;
+// `shift` is added to every exponent (tuning knob, 0 = the STR sizes).
+void str_groups(uint32_t n, int d, int* glog2, int shift = 0);
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
                          const float* hi, float2* e, uint32_t* sid, float2* nodes,
                          cudaStream_t s);
@@ -155,25 +199,32 @@ __device__ __forceinline__ bool records_complete(const RecordArena& ra) {
 }
 
 // counts[update id] (and counts_pos[sorted position], if not null); records
-// into `ra` when ra.max_blocks > 0.
-cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                         uint32_t* counts_pos, const RecordArena& ra, uint32_t* work, int sms,
-                         cudaStream_t s);
+// into `ra` when ra.max_blocks > 0.  With bv.count > 0 every query only
+// matches its own instance's subscriptions and pairs carry instance-local ids.
+// `sms` sizes the persistent grids: pass SMs x CTAs-per-SM / 8 to change the
+// default of 8 CTAs of 256 threads per SM (tuning knob).
+cudaError_t launch_count(const TreeView& t, const QueryView& q, const BatchView& bv,
+                         uint32_t flags, uint32_t* counts, uint32_t* counts_pos,
+                         const RecordArena& ra, uint32_t* work, int sms, cudaStream_t s);
 // Walking write pass; it does nothing when `ra` holds complete records (the
 // replay kernel, launched next to it, writes the pairs then).
-cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, const WriteView& w,
-                         const RecordArena& ra, uint32_t* work, Status* st, int sms,
-                         cudaStream_t s);
+cudaError_t launch_write(const TreeView& t, const QueryView& q, const BatchView& bv,
+                         uint32_t flags, const WriteView& w, const RecordArena& ra,
+                         uint32_t* work, Status* st, int sms, cudaStream_t s);
 // After the count pass: blk_list = every packet's chain, packets in plan
 // order (pkt_off must already hold the prefix of pkt_nblk).
 cudaError_t launch_block_list(const RecordArena& ra, uint32_t packets, cudaStream_t s);
 // Write pass from records: packets [p0, p1) of the plan, positions [pb, pe),
 // and (when id_filter) only updates with ids in [idb, ide).  Does nothing
 // unless `ra` holds complete records.
-cudaError_t launch_replay(const TreeView& t, const QueryView& q, const RecordArena& ra,
-                          const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
-                          bool id_filter, uint32_t idb, uint32_t ide, uint32_t* work, Status* st,
-                          int sms, cudaStream_t s);
+cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView& bv,
+                          const RecordArena& ra, const WriteView& w, uint32_t p0, uint32_t p1,
+                          uint32_t pb, uint32_t pe, bool id_filter, uint32_t idb, uint32_t ide,
+                          uint32_t* work, Status* st, int sms, cudaStream_t s);
+// pair_off[i] = offsets[upd_off[i]] for i <= count.
+cudaError_t launch_gather_offsets(const unsigned long long* offsets,
+                                  const unsigned long long* upd_off, uint32_t count,
+                                  unsigned long long* pair_off, cudaStream_t s);
 
 // ---- ddm_scan.cu ----------------------------------------------------------
 constexpr int kScanTile = 4096;

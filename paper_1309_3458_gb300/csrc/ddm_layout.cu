@@ -66,6 +66,60 @@ k_gather(int d, const uint32_t* __restrict__ vals, const float* __restrict__ lo,
   }
 }
 
+// Batched sets: one CTA per instance marks its positions.
+__global__ void k_fill_inst(const unsigned long long* __restrict__ off, uint32_t* __restrict__ inst) {
+  const unsigned long long b = off[blockIdx.x], e = off[blockIdx.x + 1];
+  for (unsigned long long i = b + threadIdx.x; i < e; i += blockDim.x) inst[i] = blockIdx.x;
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_validate_batch(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
+                 const uint32_t* __restrict__ inst, unsigned long long* __restrict__ keys,
+                 uint32_t* __restrict__ vals, Status* __restrict__ st) {
+  bool bad = false;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+    for (int k = 0; k < d; ++k) {
+      const float a = __ldg(lo + (size_t)k * cnt + i);
+      const float b = __ldg(hi + (size_t)k * cnt + i);
+      bad |= !(a <= b);
+    }
+    keys[i] = ((unsigned long long)inst[i] << 32) | float_key(__ldg(lo + i));
+    vals[i] = i;
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->err, kErrExtent);
+}
+
+__global__ void k_batch_groups(const unsigned long long* __restrict__ off, uint32_t count, int d,
+                               int k, int shift, int* __restrict__ glog2,
+                               uint32_t* __restrict__ ngroups) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < count; i += gridDim.x * blockDim.x) {
+    const uint32_t n = (uint32_t)(off[i + 1] - off[i]);
+    // strictly smaller than the previous dimension's groups, as in str_groups
+    int g = str_group_log2(n, d, k, shift);
+    for (int j = 1; j < k && g > 0; ++j) {
+      const int gp = str_group_log2(n, d, j, shift);
+      if (gp > 0 && g >= gp) g = 0;
+    }
+    glog2[i] = g;
+    ngroups[i] = g > 0 ? ((n + (1u << g) - 1) >> g) : n;  // g == 0: groups of one
+  }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_rekey_batch(const uint32_t* __restrict__ vals, const float* __restrict__ lo_k, uint32_t cnt,
+              const uint32_t* __restrict__ inst, const unsigned long long* __restrict__ off,
+              const int* __restrict__ glog2, const unsigned long long* __restrict__ gbase,
+              unsigned long long* __restrict__ keys) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+    const uint32_t b = inst[i];
+    const unsigned long long local = i - off[b];
+    const unsigned long long group = gbase[b] + (local >> glog2[b]);
+    keys[i] = (group << 32) | float_key(__ldg(lo_k + vals[i]));
+  }
+}
+
 uint32_t grid_for(uint32_t cnt, int sms) {
   uint32_t blocks = (cnt + kThreads - 1) / kThreads;
   const uint32_t cap = (uint32_t)sms * 8u;
@@ -86,6 +140,43 @@ cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const fl
                           uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
   k_gather<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, vals, lo, hi, cnt, qe, qid);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t* inst,
+                             cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  k_fill_inst<<<count, 256, 0, s>>>(off, inst);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_batch(int d, const float* lo, const float* hi, uint32_t cnt,
+                                  const uint32_t* inst, unsigned long long* keys, uint32_t* vals,
+                                  Status* st, int sms, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  k_validate_batch<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, inst, keys, vals, st);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_groups(const unsigned long long* off, uint32_t count, int d, int k,
+                                int shift, int* glog2, uint32_t* ngroups, cudaStream_t s) {
+  if (count == 0) return cudaSuccess;
+  const uint32_t blocks = (count + 255) / 256 < 1024 ? (count + 255) / 256 : 1024;
+  k_batch_groups<<<blocks, 256, 0, s>>>(off, count, d, k, shift, glog2, ngroups);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_rekey_batch(const uint32_t* vals, const float* lo_k, uint32_t cnt,
+                               const uint32_t* inst, const unsigned long long* off,
+                               const int* glog2, const unsigned long long* gbase,
+                               unsigned long long* keys, int sms, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  k_rekey_batch<<<grid_for(cnt, sms), kThreads, 0, s>>>(vals, lo_k, cnt, inst, off, glog2, gbase,
+                                                        keys);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -63,14 +63,18 @@ __device__ __forceinline__ float warp_min(float v) {
 }
 
 // D > 0: compile-time dimension count; D == 0: runtime d (up to 8).
-template <int D, bool OPEN, bool WRITE>
+// BATCH: every query matches only its instance's subscription positions, and
+// pairs carry instance-local ids.
+template <int D, bool OPEN, bool WRITE, bool BATCH>
 __global__ void __launch_bounds__(kThreads, DDM_PACKET_MIN_BLOCKS)
-k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __restrict__ counts_pos,
-          RecordArena ra, WriteView w, uint32_t* __restrict__ work, Status* __restrict__ st) {
+k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
+          uint32_t* __restrict__ counts_pos, RecordArena ra, WriteView w,
+          uint32_t* __restrict__ work, Status* __restrict__ st) {
   constexpr int DM = D > 0 ? D : DDM_MAX_DIMS;
   constexpr int DP = (DM + 1) / 2;  // dimension pairs: one 128-bit shared load each
   const int d = D > 0 ? D : t.d;
   __shared__ float4 s_q[kWarps][32][DP];
+  __shared__ uint2 s_rng[kWarps][BATCH ? 32 : 1];  // per query: its instance's positions
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
   const size_t n = t.n, total = t.total, m = q.m;
@@ -101,6 +105,21 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
     if (valid) {
       pos = q.list ? q.list[idx] : q.first + idx;
       Q = q.qid[pos];
+    }
+    // Position range of the subscriptions this query may match, and the
+    // update id written into pairs (instance-local when batched).
+    uint32_t r_lo = 0, r_hi = (uint32_t)n, Qout = Q;
+    if (BATCH && valid) {
+      const uint32_t b = bv.q_inst[pos];
+      r_lo = (uint32_t)bv.sub_off[b];
+      r_hi = (uint32_t)bv.sub_off[b + 1];
+      Qout = Q - (uint32_t)bv.upd_off[b];
+    }
+    uint32_t g_lo = 0, g_hi = (uint32_t)n;  // union of the packet's ranges
+    if (BATCH) {
+      g_lo = __reduce_min_sync(0xffffffffu, valid ? r_lo : 0xffffffffu);
+      g_hi = __reduce_max_sync(0xffffffffu, valid ? r_hi : 0u);
+      s_rng[wib][lane] = make_uint2(r_lo, r_hi);
     }
     float ql[DM], qh[DM], gl[DM], gh[DM];
 #pragma unroll
@@ -137,6 +156,7 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
       const bool cv = c < t.cnt[1];
       float bl[DM], bh[DM];
       bool ok = cv;
+      if (BATCH) ok = ok && c * 32u < g_hi && c * 32u + 32u > g_lo;
 #pragma unroll
       for (int k = 0; k < DM; ++k) {
         if (k < d) {
@@ -152,6 +172,7 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
         lm &= lm - 1u;
         // queries of the packet whose box meets this leaf's box
         bool qok = valid;
+        if (BATCH) qok = qok && (g1 + cl) * 32u < r_hi && (g1 + cl) * 32u + 32u > r_lo;
 #pragma unroll
         for (int k = 0; k < DM; ++k) {
           if (k < d) {
@@ -175,6 +196,12 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
           const int qq = __ffs(qm) - 1;
           qm &= qm - 1u;
           bool hit = iv;
+          uint32_t sub_base = 0;
+          if (BATCH) {
+            const uint2 rg = s_rng[wib][qq];
+            hit = hit & (i >= rg.x) & (i < rg.y);
+            sub_base = rg.x;
+          }
 #pragma unroll
           for (int k2 = 0; k2 < DP; ++k2) {
             if (2 * k2 < d) {
@@ -187,13 +214,13 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
           const uint32_t hb = __ballot_sync(0xffffffffu, hit);
           if (WRITE) {
             const unsigned long long o = __shfl_sync(0xffffffffu, out, qq);
-            const uint32_t Qq = __shfl_sync(0xffffffffu, Q, qq);
+            const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
             if (hit) {
               const unsigned long long at = o + __popc(hb & lt);
               if (at < w.capacity) {
                 ddm_pair pr;
                 pr.upd = Qq;
-                pr.sub = my_sid;
+                pr.sub = my_sid - sub_base;
                 w.pairs[at] = pr;
               }
             }
@@ -250,6 +277,11 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
       {
         const bool cv = (uint32_t)lane < t.cnt[lvl];
         bool ok = cv;
+        if (BATCH) {
+          const unsigned long long span = 1ull << (kLog2Fan * lvl);
+          ok = ok && (unsigned long long)lane * span < g_hi &&
+               ((unsigned long long)lane + 1) * span > g_lo;
+        }
 #pragma unroll
         for (int k = 0; k < DM; ++k) {
           if (k < d) {
@@ -276,6 +308,11 @@ k_packets(TreeView t, QueryView q, uint32_t* __restrict__ counts, uint32_t* __re
           const uint32_t ch = g * 32u + lane;
           const bool cv = ch < t.cnt[lvl - 1];
           bool ok = cv;
+          if (BATCH) {
+            const unsigned long long span = 1ull << (kLog2Fan * (lvl - 1));
+            ok = ok && (unsigned long long)ch * span < g_hi &&
+                 ((unsigned long long)ch + 1) * span > g_lo;
+          }
 #pragma unroll
           for (int k = 0; k < DM; ++k) {
             if (k < d) {
@@ -331,11 +368,11 @@ __global__ void k_block_list(RecordArena ra, uint32_t packets) {
 // pairs from qq's cursor, exactly as the walking write pass would have.
 // Cursors are relative to the range's first pair; with fewer than 2^32 pairs
 // in the range (WIDE false) they are 32-bit.
-template <bool FILTER_ID, bool WIDE>
+template <bool FILTER_ID, bool WIDE, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 6)
-k_replay(TreeView t, QueryView q, RecordArena ra, WriteView w, uint32_t p0, uint32_t p1,
-         uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide, uint32_t* __restrict__ work,
-         Status* __restrict__ st) {
+k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uint32_t p0,
+         uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
+         uint32_t* __restrict__ work, Status* __restrict__ st) {
   using Cursor = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
   const int lane = threadIdx.x & 31;
   const uint32_t lt = lanemask_lt();
@@ -368,6 +405,12 @@ k_replay(TreeView t, QueryView q, RecordArena ra, WriteView w, uint32_t p0, uint
     Cursor out = 0;
     if (valid)
       out = (Cursor)(w.start[w.by_pos ? pos : Q] - base0) + (Cursor)ra.blk_base[(size_t)blk * 32u + lane];
+    uint32_t Qout = Q, sub_base = 0;
+    if (BATCH && valid) {
+      const uint32_t b = bv.q_inst[pos];
+      Qout = Q - (uint32_t)bv.upd_off[b];
+      sub_base = (uint32_t)bv.sub_off[b];
+    }
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     if (vmask == 0u) continue;
     const bool all_valid = vmask == 0xffffffffu;
@@ -390,11 +433,12 @@ k_replay(TreeView t, QueryView q, RecordArena ra, WriteView w, uint32_t p0, uint
           if (hs[u] == 0u) continue;
           const int qq = (int)(xs[u] & 31u);
           const Cursor o = __shfl_sync(0xffffffffu, out, qq);
-          const uint32_t Qq = __shfl_sync(0xffffffffu, Q, qq);
+          const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
+          const uint32_t sb = BATCH ? __shfl_sync(0xffffffffu, sub_base, qq) : 0u;
           if ((hs[u] >> lane) & 1u) {
             ddm_pair pr;
             pr.upd = Qq;
-            pr.sub = ss[u];
+            pr.sub = ss[u] - sb;
             w.pairs[(unsigned long long)(o + (Cursor)__popc(hs[u] & lt))] = pr;
           }
           if (lane == qq) out = o + (Cursor)__popc(hs[u]);
@@ -404,10 +448,28 @@ k_replay(TreeView t, QueryView q, RecordArena ra, WriteView w, uint32_t p0, uint
   }
 }
 
+template <bool WRITE, bool BATCH>
+void dispatch_packets(int d, bool open, uint32_t blocks, cudaStream_t s, const TreeView& t,
+                      const QueryView& q, const BatchView& bv, uint32_t* counts,
+                      uint32_t* counts_pos, const RecordArena& ra, const WriteView& w,
+                      uint32_t* work, Status* st) {
+#define DDM_LAUNCH(DD, OP)                                                              \
+  k_packets<DD, OP, WRITE, BATCH><<<blocks, kThreads, 0, s>>>(t, q, bv, counts, counts_pos, \
+                                                               ra, w, work, st)
+  switch (d) {
+    case 1: open ? DDM_LAUNCH(1, true) : DDM_LAUNCH(1, false); break;
+    case 2: open ? DDM_LAUNCH(2, true) : DDM_LAUNCH(2, false); break;
+    case 3: open ? DDM_LAUNCH(3, true) : DDM_LAUNCH(3, false); break;
+    default: open ? DDM_LAUNCH(0, true) : DDM_LAUNCH(0, false); break;
+  }
+#undef DDM_LAUNCH
+}
+
 template <bool WRITE>
-cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                           uint32_t* counts_pos, const RecordArena& ra, const WriteView& w,
-                           uint32_t* work, Status* st, int sms, cudaStream_t s) {
+cudaError_t launch_packets(const TreeView& t, const QueryView& q, const BatchView& bv,
+                           uint32_t flags, uint32_t* counts, uint32_t* counts_pos,
+                           const RecordArena& ra, const WriteView& w, uint32_t* work, Status* st,
+                           int sms, cudaStream_t s) {
   if (q.nq == 0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
@@ -416,32 +478,49 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, uint32_t flags
   uint32_t blocks = (packets + kWarps - 1) / kWarps;
   const uint32_t cap = (uint32_t)sms * 8u;
   if (blocks > cap) blocks = cap;
-#define DDM_LAUNCH(DD, OP) \
-  k_packets<DD, OP, WRITE><<<blocks, kThreads, 0, s>>>(t, q, counts, counts_pos, ra, w, work, st)
-  switch (t.d) {
-    case 1: open ? DDM_LAUNCH(1, true) : DDM_LAUNCH(1, false); break;
-    case 2: open ? DDM_LAUNCH(2, true) : DDM_LAUNCH(2, false); break;
-    case 3: open ? DDM_LAUNCH(3, true) : DDM_LAUNCH(3, false); break;
-    default: open ? DDM_LAUNCH(0, true) : DDM_LAUNCH(0, false); break;
-  }
-#undef DDM_LAUNCH
+  if (bv.count)
+    dispatch_packets<WRITE, true>(t.d, open, blocks, s, t, q, bv, counts, counts_pos, ra, w, work,
+                                  st);
+  else
+    dispatch_packets<WRITE, false>(t.d, open, blocks, s, t, q, bv, counts, counts_pos, ra, w,
+                                   work, st);
   note_launches(1);
   return cudaGetLastError();
 }
 
-}  // namespace
-
-cudaError_t launch_count(const TreeView& t, const QueryView& q, uint32_t flags, uint32_t* counts,
-                         uint32_t* counts_pos, const RecordArena& ra, uint32_t* work, int sms,
-                         cudaStream_t s) {
-  WriteView w{};
-  return launch_packets<false>(t, q, flags, counts, counts_pos, ra, w, work, nullptr, sms, s);
+template <bool FILTER_ID, bool BATCH>
+void dispatch_replay(bool wide, uint32_t blocks, cudaStream_t s, const TreeView& t,
+                     const QueryView& q, const BatchView& bv, const RecordArena& ra,
+                     const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
+                     uint32_t idb, uint32_t ide, uint32_t* work, Status* st) {
+  if (wide)
+    k_replay<FILTER_ID, true, BATCH><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe,
+                                                                 idb, ide, work, st);
+  else
+    k_replay<FILTER_ID, false, BATCH><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe,
+                                                                  idb, ide, work, st);
 }
 
-cudaError_t launch_write(const TreeView& t, const QueryView& q, uint32_t flags, const WriteView& w,
-                         const RecordArena& ra, uint32_t* work, Status* st, int sms,
-                         cudaStream_t s) {
-  return launch_packets<true>(t, q, flags, nullptr, nullptr, ra, w, work, st, sms, s);
+__global__ void k_gather_offsets(const unsigned long long* __restrict__ offsets,
+                                 const unsigned long long* __restrict__ upd_off, uint32_t count,
+                                 unsigned long long* __restrict__ pair_off) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += gridDim.x * blockDim.x)
+    pair_off[i] = offsets[upd_off[i]];
+}
+
+}  // namespace
+
+cudaError_t launch_count(const TreeView& t, const QueryView& q, const BatchView& bv,
+                         uint32_t flags, uint32_t* counts, uint32_t* counts_pos,
+                         const RecordArena& ra, uint32_t* work, int sms, cudaStream_t s) {
+  WriteView w{};
+  return launch_packets<false>(t, q, bv, flags, counts, counts_pos, ra, w, work, nullptr, sms, s);
+}
+
+cudaError_t launch_write(const TreeView& t, const QueryView& q, const BatchView& bv,
+                         uint32_t flags, const WriteView& w, const RecordArena& ra,
+                         uint32_t* work, Status* st, int sms, cudaStream_t s) {
+  return launch_packets<true>(t, q, bv, flags, nullptr, nullptr, ra, w, work, st, sms, s);
 }
 
 cudaError_t launch_block_list(const RecordArena& ra, uint32_t packets, cudaStream_t s) {
@@ -453,10 +532,10 @@ cudaError_t launch_block_list(const RecordArena& ra, uint32_t packets, cudaStrea
   return cudaGetLastError();
 }
 
-cudaError_t launch_replay(const TreeView& t, const QueryView& q, const RecordArena& ra,
-                          const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
-                          bool id_filter, uint32_t idb, uint32_t ide, uint32_t* work, Status* st,
-                          int sms, cudaStream_t s) {
+cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView& bv,
+                          const RecordArena& ra, const WriteView& w, uint32_t p0, uint32_t p1,
+                          uint32_t pb, uint32_t pe, bool id_filter, uint32_t idb, uint32_t ide,
+                          uint32_t* work, Status* st, int sms, cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
@@ -464,16 +543,25 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const RecordAre
   // Cursors fit 32 bits when the range's pairs do; the capacity bounds them.
   const bool wide = w.capacity > 0xffffffffull;
   if (id_filter) {
-    if (wide)
-      k_replay<true, true><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+    if (bv.count)
+      dispatch_replay<true, true>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
     else
-      k_replay<true, false><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+      dispatch_replay<true, false>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
   } else {
-    if (wide)
-      k_replay<false, true><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+    if (bv.count)
+      dispatch_replay<false, true>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
     else
-      k_replay<false, false><<<blocks, kThreads, 0, s>>>(t, q, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+      dispatch_replay<false, false>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
   }
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_offsets(const unsigned long long* offsets,
+                                  const unsigned long long* upd_off, uint32_t count,
+                                  unsigned long long* pair_off, cudaStream_t s) {
+  const uint32_t blocks = (count + 256) / 256 < 1024 ? (count + 256) / 256 : 1024;
+  k_gather_offsets<<<blocks, 256, 0, s>>>(offsets, upd_off, count, pair_off);
   note_launches(1);
   return cudaGetLastError();
 }

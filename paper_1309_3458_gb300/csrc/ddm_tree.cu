@@ -126,19 +126,14 @@ void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* tota
   *total = acc;
 }
 
-// Sort-tile-recursive split: with nb = n/32 leaves, each dimension gets about
-// nb^(1/d) slabs; dimension k >= 1 is re-sorted inside groups of
-// 32 * nb^((d-k)/d) positions, rounded to a power of two.  glog2[k] = 0 means
-// no re-sort (groups would not be smaller than the previous ones or would
-// hold a single leaf).
-void str_groups(uint32_t n, int d, int* glog2) {
+// Group exponents of the per-dimension re-sorts (str_group_log2), kept
+// strictly decreasing so that every re-sort refines the previous groups.
+void str_groups(uint32_t n, int d, int* glog2, int shift) {
   for (int k = 0; k < DDM_MAX_DIMS; ++k) glog2[k] = 0;
-  const double nb = std::ceil((double)n / kFan);
   int prev = 64;
   for (int k = 1; k < d; ++k) {
-    const double G = kFan * std::pow(nb, (double)(d - k) / d);
-    const int g = (int)std::floor(std::log2(G) + 0.5);
-    if (g >= 6 && g < prev && ((uint64_t)1 << g) < n) {
+    const int g = str_group_log2(n, d, k, shift);
+    if (g > 0 && g < prev) {
       glog2[k] = g;
       prev = g;
     }

@@ -197,3 +197,22 @@ def make(name: str, scale: float = 1.0) -> Arrays:
     if c["kind"] == "uniform":
         return uniform_fixed_length(n, m, c["d"], c["alpha"], c["seed"])
     return clustered_lognormal(n, m, c["d"], c["alpha"], c["seed"])
+
+
+def concat_instances(instances) -> Tuple[np.ndarray, np.ndarray, np.ndarray,
+                                          np.ndarray, np.ndarray, np.ndarray]:
+    """Concatenate independent problems for the batched call: returns
+    ``(upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub_off)`` with the sets laid
+    out instance after instance (SoA over the whole batch) and uint64 offset
+    arrays of ``count + 1`` entries."""
+    d = instances[0][0].shape[0]
+    ms = [a[0].shape[1] for a in instances]
+    ns = [a[2].shape[1] for a in instances]
+    upd_off = np.concatenate([[0], np.cumsum(ms)]).astype(np.uint64)
+    sub_off = np.concatenate([[0], np.cumsum(ns)]).astype(np.uint64)
+
+    def cat(i):
+        parts = [a[i] for a in instances]
+        return np.ascontiguousarray(np.concatenate(parts, axis=1)) if parts else np.zeros((d, 0), np.float32)
+
+    return cat(0), cat(1), upd_off, cat(2), cat(3), sub_off
