@@ -64,6 +64,9 @@ def parse():
                     help="skip the batched-instances comparison (4,096 problems)")
     ap.add_argument("--batched-only", action="store_true",
                     help="run only the batched-instances comparison")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
+    ap.add_argument("--serving-only", action="store_true", help="run only the serving run")
+    ap.add_argument("--serving-seconds", type=float, default=2.0)
     return ap.parse_args()
 
 
@@ -274,6 +277,66 @@ def batched_section(reps: int = 3):
         ddm.ddm_destroy(ctx)
 
 
+def serving_section(seconds: float = 2.0, slots: int = 8):
+    """Serving: d = 2, 1e6 resident subscription regions (side 1e3, i.e.
+    alpha = 1 at N = 1e6) moving every 10 ms by a Gaussian random walk
+    (sigma = 1e-3 L, reflected); 64 federates send match requests with
+    Poisson arrivals (2,000 per second in total) and update-set sizes
+    log-uniform in [1e3, 1e6]; continuous batching over `slots` streams with
+    admission by a device-memory budget."""
+    import torch
+
+    from paper_1309_3458_gb300 import serving as S
+    d, n, l = 2, 1_000_000, 1000.0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2026)
+    lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
+    hi = (lo + l).contiguous()
+    regions = S.ResidentRegions(lo, hi)
+    state = {"lo": lo, "hi": hi}
+    mg = torch.Generator(device="cuda")
+    mg.manual_seed(7)
+
+    def mover(step):
+        state["lo"], state["hi"] = S.random_walk(state["lo"], state["hi"], 1000.0, mg)
+        return state["lo"], state["hi"]
+
+    sched = S.poisson_schedule(rate=2000.0, duration=seconds, federates=64, size_lo=1000,
+                               size_hi=1_000_000, seed=1)
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(free * 0.4)
+    srv = S.Server(regions, l, slots=slots, budget_bytes=budget, pair_capacity=1 << 26)
+    try:
+        t0 = time.perf_counter()
+        done = srv.run(sched, mover=mover, step_s=0.010)
+        wall = time.perf_counter() - t0
+    finally:
+        srv.close()
+    # plain: the first requests one after another on one context, no overlap
+    plain_n = min(len(sched), 400)
+    plain_sched = [S.Request(rid=r.rid, federate=r.federate, arrival=0.0, size=r.size,
+                             seed=r.seed) for r in sched[:plain_n]]
+    one = S.Server(regions, l, slots=1, budget_bytes=budget, pair_capacity=1 << 26)
+    try:
+        t0 = time.perf_counter()
+        pdone = one.run(plain_sched, mover=None)
+        plain_wall = time.perf_counter() - t0
+    finally:
+        one.close()
+        regions.close()
+    out = S.summary(done, wall)
+    plain_q = sum(r.size for r in pdone) / plain_wall
+    out["plain_one_at_a_time"] = {"requests": plain_n, "wall_s": plain_wall,
+                                  "queries_per_s": plain_q,
+                                  "pairs_per_s": sum(r.K for r in pdone) / plain_wall}
+    out["served_over_plain"] = out["queries_per_s"] / plain_q
+    out.update({"workload": "d=2, 1e6 moving regions, 64 federates, 2000 req/s Poisson, "
+                            "sizes log-uniform [1e3, 1e6]",
+                "slots": slots, "budget_gb": budget / 1e9, "offered_s": seconds,
+                "steps": max(r.step for r in done) if done else 0})
+    return out
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -309,6 +372,9 @@ def main():
     torch.cuda.set_device(local)
     if args.batched_only:
         print(json.dumps({"batched": batched_section()}), flush=True)
+        return
+    if args.serving_only:
+        print(json.dumps({"serving": serving_section(args.serving_seconds)}), flush=True)
         return
     if world > 1:
         tdist.init_process_group("nccl")
@@ -438,6 +504,11 @@ def main():
         torch.cuda.empty_cache()
         batched = batched_section()
 
+    serving = None
+    if not args.no_serving and world == 1:
+        torch.cuda.empty_cache()
+        serving = serving_section(args.serving_seconds)
+
     cpu = None
     if not args.no_cpu and world == 1:
         cpu = cpu_oracle_sample(arrays, args.cpu_seconds)
@@ -483,6 +554,7 @@ def main():
         "cpu_baseline": cpu,
         "clocks": clocks,
         "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line), flush=True)
 

@@ -139,6 +139,26 @@ int ddm_match_range(ddm_ctx *ctx, int d,
 int ddm_build(ddm_ctx *ctx, int d, const float *sub_lo, const float *sub_hi,
               uint32_t n, void *stream);
 
+/* In-place refit after the subscriptions moved (dynamic interval
+ * management, Section IV): the subscriptions keep their ids and their
+ * position in the tree; sub_lo / sub_hi hold their new coordinates (same d
+ * and n as the build).  Every node's per-dimension minlower / maxupper is
+ * recomputed, so queries stay exact whatever the movement (the tree may
+ * prune less once the order no longer follows the lower bounds; a new
+ * ddm_build restores it).  Drops the current plan.  Synchronises `stream`.
+ * Errors: DDM_ERR_STATE (no own single-problem tree: none built, attached,
+ * or batched), DDM_ERR_ARG, DDM_ERR_EXTENT, DDM_ERR_CUDA. */
+int ddm_refit(ddm_ctx *ctx, const float *sub_lo, const float *sub_hi, void *stream);
+
+/* Let `ctx` query the tree built in `src` (same device) without copying it:
+ * ctx's plans and writes use its own workspace and src's tree, so several
+ * contexts can serve requests against one resident tree on separate
+ * streams.  The tree must not be rebuilt, refitted or destroyed while an
+ * attached context uses it; after a rebuild of src, attach again.  A later
+ * ddm_build on ctx makes it own a tree again.  Errors: DDM_ERR_ARG,
+ * DDM_ERR_STATE (src has no single-problem tree). */
+int ddm_attach(ddm_ctx *ctx, const ddm_ctx *src);
+
 /* Counting pass (Alg. 4 per update, without output) for all m updates
  * against the built tree, and the exclusive prefix sum of the per-update
  * counts.  offsets (optional, device, m + 1 entries of uint64) receives the

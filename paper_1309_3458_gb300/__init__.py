@@ -51,6 +51,8 @@ SIGNATURES = {
     "ddm_match_range": (_i, [_vp, _i] + _SET + _SET + [_u32, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_build": (_i, [_vp, _i, _vp, _vp, _u32, _vp]),
     "ddm_plan": (_i, [_vp, _vp, _vp, _u32, _u32, _vp, _pu64, _vp]),
+    "ddm_refit": (_i, [_vp, _vp, _vp, _vp]),
+    "ddm_attach": (_i, [_vp, _vp]),
     "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
     "ddm_plan_order": (_i, [_vp, _vp, _vp, _vp]),
@@ -180,6 +182,14 @@ def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, up
 def ddm_build(ctx: int, sub_lo, sub_hi, stream=None) -> None:
     d, sl, sh, n = _set(sub_lo, sub_hi)
     _check(lib().ddm_build(ctx, d, sl, sh, n, _stream(stream)), "ddm_build")
+
+
+def ddm_refit(ctx: int, sub_lo, sub_hi, stream=None) -> None:
+    _check(lib().ddm_refit(ctx, _ptr(sub_lo), _ptr(sub_hi), _stream(stream)), "ddm_refit")
+
+
+def ddm_attach(ctx: int, src: int) -> None:
+    _check(lib().ddm_attach(ctx, src), "ddm_attach")
 
 
 def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,

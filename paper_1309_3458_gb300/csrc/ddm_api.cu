@@ -57,6 +57,7 @@ struct ddm_ctx {
   bool replay_on = true;        // record / replay write pass allowed
 
   bool built = false;
+  bool attached = false;        // tree borrowed from another context (ddm_attach)
   TreeView tree{};
   bool planned = false;
   const float* ulo = nullptr;
@@ -249,6 +250,7 @@ int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
 int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n, cudaStream_t s,
                 const BatchSet* bs = nullptr) {
   c->built = false;
+  c->attached = false;
   if (!bs) c->bv = BatchView{};
   c->planned = false;
   TreeView t{};
@@ -757,6 +759,41 @@ int ddm_batch_match_async(ddm_ctx* c, int d, uint32_t count, const float* upd_lo
   return batch_impl(c, d, count, upd_lo, upd_hi, upd_off, m_total, sub_lo, sub_hi, sub_off,
                     n_total, flags, pairs, capacity, pair_off, nullptr, k_dev, err_dev, stream,
                     false);
+}
+
+int ddm_refit(ddm_ctx* c, const float* sub_lo, const float* sub_hi, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->built || c->attached || c->bv.count) return DDM_ERR_STATE;
+  if (c->tree.n > 0 && (!sub_lo || !sub_hi)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  c->planned = false;
+  if (c->tree.n > 0) {
+    DDM_CUDA(launch_validate(c->tree.d, sub_lo, sub_hi, c->tree.n, nullptr, nullptr, 0, c->st_dev,
+                             c->sms, s));
+    // Same order, new coordinates: gather through the tree's own id column and
+    // recompute every node's per-dimension (minlower, maxupper).
+    DDM_CUDA(launch_build(c->tree, c->tree.sid, sub_lo, sub_hi, static_cast<float2*>(c->e.p),
+                          static_cast<uint32_t*>(c->sid.p), static_cast<float2*>(c->nodes.p), s));
+  }
+  DDM_TRY(sync_status(c, s));
+  const int rc = status_code(*c->st_host);
+  if (rc != DDM_OK) c->built = false;
+  return rc;
+}
+
+int ddm_attach(ddm_ctx* c, const ddm_ctx* src) {
+  if (!c || !src || c == src) return DDM_ERR_ARG;
+  if (!src->built || src->bv.count) return DDM_ERR_STATE;
+  if (c->device != src->device) return DDM_ERR_ARG;
+  c->tree = src->tree;
+  c->bv = BatchView{};
+  c->built = true;
+  c->attached = true;
+  c->planned = false;
+  return DDM_OK;
 }
 
 int ddm_tree_shape(ddm_ctx* c, int* levels, uint32_t* counts, uint32_t* total) {

@@ -1,0 +1,122 @@
+"""Serving: requests admitted while others run overlap on the GPU, and each
+request's pairs are exactly those of the same request run alone against the
+same (pinned) version of the moving subscriptions."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_1309_3458_gb300 as ddm
+from paper_1309_3458_gb300 import serving as S
+from tests.helpers import keys
+
+pytestmark = pytest.mark.gpu
+
+
+def test_refit_matches_fresh_build():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1309_3458_gb300 import workloads as W
+    a = W.uniform_fixed_length(30000, 20000, 2, 20.0, seed=1)
+    b = W.uniform_fixed_length(30000, 20000, 2, 20.0, seed=2)   # "moved" subscriptions
+    ctx = ddm.ddm_create(0)
+    try:
+        U = [torch.from_numpy(x).cuda() for x in a]
+        ddm.ddm_build(ctx, U[2], U[3])
+        slo, shi = torch.from_numpy(b[2]).cuda(), torch.from_numpy(b[3]).cuda()
+        ddm.ddm_refit(ctx, slo, shi)
+        K = ddm.ddm_plan(ctx, U[0], U[1])
+        buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+        ddm.ddm_write(ctx, 0, 20000, buf)
+        got = buf[:K].cpu().numpy().view(np.uint32)
+    finally:
+        ddm.ddm_destroy(ctx)
+    Ko, ou, os_ = oracle.itm_pairs(a[0], a[1], b[2], b[3])
+    assert K == Ko
+    assert np.array_equal(got[:, 0], ou)
+    assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(ou, os_)))
+
+
+def test_serving_mix_equals_alone():
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    d, n, l = 2, 20000, 5000.0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(7)
+    lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
+    hi = (lo + l).contiguous()
+    regions = S.ResidentRegions(lo, hi, keep_history=True)
+    state = {"lo": lo, "hi": hi}
+    mg = torch.Generator(device="cuda")
+    mg.manual_seed(11)
+
+    def mover(step):
+        state["lo"], state["hi"] = S.random_walk(state["lo"], state["hi"], 1000.0, mg)
+        return state["lo"], state["hi"]
+
+    sched = S.poisson_schedule(rate=5000.0, duration=0.012, federates=8, size_lo=100,
+                               size_hi=3000, seed=3)
+    assert len(sched) >= 30
+    srv = S.Server(regions, l, slots=4, pair_capacity=1 << 20, keep_pairs=True)
+    try:
+        done = srv.run(sched, mover=mover, step_s=0.002)
+    finally:
+        srv.close()
+    # requests overlapped on the device
+    overlap = any(a.admitted < b.done and b.admitted < a.done
+                  for i, a in enumerate(done) for b in done[i + 1:])
+    assert overlap
+    assert len({r.step for r in done}) >= 2          # the regions moved during the run
+    ctx = ddm.ddm_create(0)
+    try:
+        for r in done:
+            plo, phi = regions.history[r.step]
+            ulo, uhi = S.request_updates(r.seed, r.size, d, l)
+            K = ddm.ddm_count(ctx, ulo, uhi, plo, phi)
+            assert K == r.K
+            buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+            ddm.ddm_match(ctx, ulo, uhi, plo, phi, buf)
+            alone = buf[:K].cpu().numpy().view(np.uint32)
+            assert np.array_equal(np.sort(keys(r.pairs[:, 0], r.pairs[:, 1])),
+                                  np.sort(keys(alone[:, 0], alone[:, 1])))
+        # and against the oracle for a few of them
+        for r in done[:5]:
+            plo, phi = regions.history[r.step]
+            ulo, uhi = S.request_updates(r.seed, r.size, d, l)
+            Ko, ou, os_ = oracle.itm_pairs(ulo.cpu().numpy(), uhi.cpu().numpy(),
+                                           plo.cpu().numpy(), phi.cpu().numpy())
+            assert Ko == r.K
+            assert np.array_equal(np.sort(keys(r.pairs[:, 0], r.pairs[:, 1])),
+                                  np.sort(keys(ou, os_)))
+    finally:
+        ddm.ddm_destroy(ctx)
+        regions.close()
+
+
+def test_refit_state_errors():
+    import torch
+    ctx = ddm.ddm_create(0)
+    other = ddm.ddm_create(0)
+    try:
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_refit(ctx, None, None)
+        assert e.value.code == ddm.DDM_ERR_STATE
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_attach(other, ctx)
+        assert e.value.code == ddm.DDM_ERR_STATE
+        lo = torch.zeros((2, 64), device="cuda")
+        hi = torch.ones((2, 64), device="cuda")
+        ddm.ddm_build(ctx, lo, hi)
+        ddm.ddm_attach(other, ctx)
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_refit(other, lo, hi)      # attached contexts do not own the tree
+        assert e.value.code == ddm.DDM_ERR_STATE
+        bad = hi.clone()
+        bad[1, 5] = -1.0
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_refit(ctx, lo, bad)
+        assert e.value.code == ddm.DDM_ERR_EXTENT
+    finally:
+        ddm.ddm_destroy(other)
+        ddm.ddm_destroy(ctx)
