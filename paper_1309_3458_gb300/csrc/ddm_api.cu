@@ -42,7 +42,7 @@ struct ddm_ctx {
   // range selection for ddm_write over a sub-range of updates
   DevBuf sel_offs, sel_list;
   // replay records of the count pass
-  DevBuf rec, blk_next, blk_count, blk_pkt, blk_base, pkt_first, pkt_nblk, pkt_off, blk_list,
+  DevBuf rec, blk_next, blk_count, blk_pkt, pkt_first, pkt_nblk, pkt_off, blk_list,
       blk_counter;
   uint64_t replay_budget = 0;   // bytes; 0 = never record
   uint32_t rec_blocks = 0;      // blocks of the current arena
@@ -319,28 +319,26 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   c->arena = RecordArena{};
   if (record && c->replay_on && m > 0 && c->tree.n > 0 && c->replay_budget > 0) {
     const uint32_t packets = (m + 31) / 32;
-    // bytes per block: records, next/count/packet/list entries, 32 base counts
-    const uint64_t per_block = (uint64_t)kRecBlock * sizeof(uint2) + 36 * sizeof(uint32_t);
+    // bytes per block: records (three words each), next/count/packet/list entries
+    const uint64_t per_block = (uint64_t)kRecBlock * 3 * sizeof(uint32_t) + 4 * sizeof(uint32_t);
     uint64_t want = c->rec_hint ? (uint64_t)c->rec_hint + c->rec_hint / 8 + 64 : 2ull * packets;
     const uint64_t cap_blocks = c->replay_budget / per_block;
     if (want > cap_blocks) want = cap_blocks;
     if (want > 0xfffffff0ull) want = 0xfffffff0ull;
-    if (want > 0 && ensure(c, c->rec, (size_t)want * kRecBlock * sizeof(uint2)) == DDM_OK &&
+    if (want > 0 && ensure(c, c->rec, (size_t)want * kRecBlock * 3 * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_next, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_count, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_pkt, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
-        ensure(c, c->blk_base, (size_t)want * 32 * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_list, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_first, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_nblk, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_off, ((size_t)packets + 1) * sizeof(unsigned long long)) == DDM_OK &&
         ensure(c, c->blk_counter, 2 * sizeof(uint32_t)) == DDM_OK) {
-      c->arena.rec = static_cast<uint2*>(c->rec.p);
+      c->arena.rec = static_cast<uint32_t*>(c->rec.p);
       c->arena.blk_next = static_cast<uint32_t*>(c->blk_next.p);
       c->arena.blk_count = static_cast<uint32_t*>(c->blk_count.p);
       c->arena.pkt_first = static_cast<uint32_t*>(c->pkt_first.p);
       c->arena.blk_pkt = static_cast<uint32_t*>(c->blk_pkt.p);
-      c->arena.blk_base = static_cast<uint32_t*>(c->blk_base.p);
       c->arena.blk_list = static_cast<uint32_t*>(c->blk_list.p);
       c->arena.pkt_nblk = static_cast<uint32_t*>(c->pkt_nblk.p);
       c->arena.pkt_off = static_cast<unsigned long long*>(c->pkt_off.p);
@@ -504,7 +502,7 @@ int ddm_destroy(ddm_ctx* c) {
                     &c->counters, &c->e, &c->sid, &c->nodes, &c->qe, &c->qid, &c->counts,
                     &c->counts_pos, &c->offsets, &c->pos_offsets, &c->sums, &c->work,
                     &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
-                    &c->blk_pkt, &c->blk_base, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
+                    &c->blk_pkt, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
                     &c->blk_list, &c->blk_counter, &c->inst_s, &c->inst_u, &c->bglog2,
                     &c->bngroups, &c->bgbase})
     release(*b);

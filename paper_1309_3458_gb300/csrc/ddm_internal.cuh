@@ -168,22 +168,22 @@ cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_h
 
 // ---- ddm_query.cu ---------------------------------------------------------
 // Replay records.  While counting, every (query, leaf) test of a packet
-// that has hits is stored as one record: x = leaf << 5 | query lane,
-// y = hit mask over the leaf's 32 subscriptions.  Records of a packet are
-// kept in walk order (leaf by leaf, query lanes ascending within a leaf), in
-// a chain of fixed-size blocks taken from a shared arena.  Each block also
-// stores its packet and, per query lane, the matches the packet had before
-// the block, so every block can be expanded on its own: after counting, the
-// blocks are listed in plan order and the write pass expands any range of
-// them in parallel, instead of walking the tree again.
-constexpr uint32_t kRecBlock = 512;       // records per block (4 KiB)
+// that has hits is stored as one record of three words: x = leaf << 5 |
+// query lane, hit mask over the leaf's 32 subscriptions, and the query's
+// matches before this leaf (so the record knows where its pairs go in the
+// query's output).  Records of a packet are kept in walk order (leaf by
+// leaf, query lanes ascending within a leaf), in a chain of fixed-size
+// blocks taken from a shared arena; a block stores its packet.  After
+// counting, the blocks are listed in plan order and the write pass expands
+// any range of them, every record independently, instead of walking the
+// tree again.
+constexpr uint32_t kRecBlock = 512;       // records per block (3 x 2 KiB, one array per word)
 constexpr uint32_t kNoBlock = 0xffffffffu;
 struct RecordArena {
-  uint2* rec;              // [max_blocks * kRecBlock]
+  uint32_t* rec;           // [max_blocks][3][kRecBlock]: x, hit mask, matches before
   uint32_t* blk_next;      // [max_blocks] next block of the packet, or kNoBlock
   uint32_t* blk_count;     // [max_blocks] records in the block
   uint32_t* blk_pkt;       // [max_blocks] packet of the block
-  uint32_t* blk_base;      // [max_blocks * 32] per query lane: matches before the block
   uint32_t* pkt_first;     // [packets] first block of each packet, or kNoBlock
   uint32_t* pkt_nblk;      // [packets] blocks of each packet
   unsigned long long* pkt_off;  // [packets + 1] exclusive prefix of pkt_nblk

@@ -34,6 +34,12 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Count pass: a leaf tested by at least this many of the packet's queries is
+// evaluated with the loops swapped (lane = query, loop over the leaf's 32
+// subscriptions), which costs the same whatever the number of queries.
+#ifndef DDM_TRANSPOSE_MIN
+#define DDM_TRANSPOSE_MIN 20
+#endif
 // Resident 256-thread blocks per SM the packet kernels are compiled for.
 #ifndef DDM_PACKET_MIN_BLOCKS
 #define DDM_PACKET_MIN_BLOCKS 4
@@ -74,6 +80,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
   constexpr int DP = (DM + 1) / 2;  // dimension pairs: one 128-bit shared load each
   const int d = D > 0 ? D : t.d;
   __shared__ float4 s_q[kWarps][32][DP];
+  __shared__ float4 s_e[WRITE ? 1 : kWarps][32][DP];  // count pass: a leaf's subscriptions
   __shared__ uint2 s_rng[kWarps][BATCH ? 32 : 1];  // per query: its instance's positions
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -192,6 +199,46 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
         uint32_t my_sid = 0;
         if (WRITE && iv) my_sid = t.sid[i];
         uint32_t my_hb = 0;  // count pass: this lane's query's hit mask in the leaf
+        if (!WRITE && __popc(qm) >= DDM_TRANSPOSE_MIN) {
+          // Swapped loops: stage the leaf's subscriptions, then every lane
+          // tests its own query against all 32 of them (the same segment
+          // tests of Alg. 1 in every dimension, in the opposite order).
+#pragma unroll
+          for (int k2 = 0; k2 < DP; ++k2) {
+            if (2 * k2 < d)
+              s_e[wib][lane][k2] = make_float4(ev[2 * k2].x, ev[2 * k2].y,
+                                               2 * k2 + 1 < d ? ev[2 * k2 + 1].x : 0.f,
+                                               2 * k2 + 1 < d ? ev[2 * k2 + 1].y : 0.f);
+          }
+          __syncwarp();
+          uint32_t hbm = 0;
+#pragma unroll 8
+          for (int e = 0; e < 32; ++e) {
+            bool hit = true;
+#pragma unroll
+            for (int k2 = 0; k2 < DP; ++k2) {
+              if (2 * k2 < d) {
+                const float4 b = s_e[wib][e][k2];
+                hit = hit & le<OPEN>(b.x, qh[2 * k2]) & le<OPEN>(ql[2 * k2], b.y);
+                if (2 * k2 + 1 < d)
+                  hit = hit & le<OPEN>(b.z, qh[2 * k2 + 1]) & le<OPEN>(ql[2 * k2 + 1], b.w);
+              }
+            }
+            hbm |= (hit ? 1u : 0u) << e;
+          }
+          __syncwarp();
+          hbm &= __ballot_sync(0xffffffffu, iv);  // padding lanes of the last leaf
+          if (BATCH) {  // only this query's instance: positions [r_lo, r_hi)
+            const uint32_t base = (g1 + cl) * 32u;
+            const uint32_t a = r_lo > base ? min(r_lo - base, 32u) : 0u;
+            const uint32_t b = r_hi > base ? min(r_hi - base, 32u) : 0u;
+            const uint32_t upto_b = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+            const uint32_t upto_a = a >= 32u ? 0xffffffffu : ((1u << a) - 1u);
+            hbm &= upto_b & ~upto_a;
+          }
+          my_hb = ((qm >> lane) & 1u) ? hbm : 0u;
+          qm = 0u;
+        }
         while (qm) {
           const int qq = __ffs(qm) - 1;
           qm &= qm - 1u;
@@ -251,15 +298,17 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
                     }
                     ra.blk_pkt[b] = p;
                   }
-                  ra.blk_base[(size_t)b * 32u + lane] = cnt;  // matches before this leaf
                   cur_blk = b;
                 }
               }
               fill = 0;
             }
-            if (rec_write && my_hb != 0u)
-              ra.rec[(size_t)cur_blk * kRecBlock + fill + __popc(rm & lt)] =
-                  make_uint2(((g1 + cl) << 5) | (uint32_t)lane, my_hb);
+            if (rec_write && my_hb != 0u) {
+              uint32_t* r = ra.rec + (size_t)cur_blk * (3u * kRecBlock) + fill + __popc(rm & lt);
+              r[0] = ((g1 + cl) << 5) | (uint32_t)lane;
+              r[kRecBlock] = my_hb;
+              r[2u * kRecBlock] = cnt;  // this query's matches before the leaf
+            }
             fill += k;
           }
         }
@@ -359,23 +408,34 @@ __global__ void k_block_list(RecordArena ra, uint32_t packets) {
 // Write pass from the records of the count pass.  Work unit: one record
 // block (up to 512 records of one packet), taken from the plan-order block
 // list, so uneven packets spread over the whole GPU.  A warp loads the
-// block's packet queries, starts each query's cursor at its output offset
-// plus the matches it had before the block, and expands the records 32 at a
-// time (one coalesced load) in groups of 8: the subscription ids of the 8
-// records are loaded first (independent loads in flight together), then the
-// records are written in order.  For a record of query lane qq and leaf g
-// the lanes holding a set bit of the hit mask write (update, subscription)
-// pairs from qq's cursor, exactly as the walking write pass would have.
-// Cursors are relative to the range's first pair; with fewer than 2^32 pairs
-// in the range (WIDE false) they are 32-bit.
+// block's packet queries (their output offsets) and takes the records 32 at
+// a time, one per lane.  Each lane works out where its record's pairs go
+// (its query's offset plus the matches the count pass had found before the
+// record); an exclusive scan over the lanes gives every pair of the 32
+// records a slot in a per-warp staging buffer in shared memory, into which
+// each lane writes its own record's pairs (one per set bit of the hit mask)
+// together with their output positions.  The warp then copies the buffer
+// out, lane = pair: each store instruction writes 32 consecutive staged
+// pairs, which form a few contiguous runs of the output -- the positions the
+// walking write pass would use.  Positions are relative to the range's first
+// pair; with fewer than 2^32 pairs in the range (WIDE false) they are 32-bit.
+// Staged pairs per warp: 32 records hold at most 1,024 pairs, so two rounds
+// at most (four with 64-bit positions).
+template <bool WIDE>
+struct ReplayBuf {
+  static constexpr int kPairs = WIDE ? 256 : 512;
+};
+
 template <bool FILTER_ID, bool WIDE, bool BATCH>
-__global__ void __launch_bounds__(kThreads, 6)
+__global__ void __launch_bounds__(kThreads, 4)
 k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uint32_t p0,
          uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
          uint32_t* __restrict__ work, Status* __restrict__ st) {
   using Cursor = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-  const int lane = threadIdx.x & 31;
-  const uint32_t lt = lanemask_lt();
+  constexpr int kReplayBuf = ReplayBuf<WIDE>::kPairs;
+  __shared__ ddm_pair s_pair[kWarps][kReplayBuf];
+  __shared__ Cursor s_pos[kWarps][kReplayBuf];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   if (!records_complete(ra)) return;  // the walking write pass handles this range
   const unsigned long long base0 = w.start[w.b_idx];
   const unsigned long long need = w.start[w.e_idx] - base0;
@@ -383,10 +443,10 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     st->K = need;
     if (need > w.capacity) atomicOr(&st->err, kErrCapacity);
   }
-  // Pair positions are bounded by construction: every cursor starts at its
-  // update's offset plus the matches before the block and advances by the
-  // popcounts that the count pass summed into that update's count, so all
-  // writes stay below need <= capacity.
+  // Pair positions are bounded by construction: a record's pairs go to its
+  // update's offset plus the matches the count pass had found before it, and
+  // the update's count is the sum of its records' popcounts, so all writes
+  // stay below need <= capacity.
   if (need > w.capacity) return;
   if (!WIDE && need > 0xffffffffull) return;  // host picks WIDE for such ranges
   const unsigned long long i0 = ra.pkt_off[p0], i1 = ra.pkt_off[p1];
@@ -403,8 +463,7 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     if (valid) Q = q.qid[pos];
     if (FILTER_ID) valid = valid && Q >= idb && Q < ide;
     Cursor out = 0;
-    if (valid)
-      out = (Cursor)(w.start[w.by_pos ? pos : Q] - base0) + (Cursor)ra.blk_base[(size_t)blk * 32u + lane];
+    if (valid) out = (Cursor)(w.start[w.by_pos ? pos : Q] - base0);
     uint32_t Qout = Q, sub_base = 0;
     if (BATCH && valid) {
       const uint32_t b = bv.q_inst[pos];
@@ -413,36 +472,49 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     }
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     if (vmask == 0u) continue;
-    const bool all_valid = vmask == 0xffffffffu;
     const uint32_t nrec = ra.blk_count[blk];
-    const uint2* rec = ra.rec + (size_t)blk * kRecBlock;
+    const uint32_t* rec = ra.rec + (size_t)blk * (3u * kRecBlock);
     for (uint32_t r0 = 0; r0 < nrec; r0 += 32u) {
-      const uint2 mine = r0 + lane < nrec ? rec[r0 + lane] : make_uint2(0u, 0u);
-      const uint32_t cnt = min(32u, nrec - r0);
-      for (uint32_t j0 = 0; j0 < cnt; j0 += 8u) {
-        uint32_t xs[8], hs[8], ss[8];
+      const bool rv = r0 + lane < nrec;
+      const uint32_t x = rv ? rec[r0 + lane] : 0u;
+      uint32_t hb = rv ? rec[kRecBlock + r0 + lane] : 0u;
+      const uint32_t bef = rv ? rec[2u * kRecBlock + r0 + lane] : 0u;
+      const int qq = (int)(x & 31u);
+      if (!((vmask >> qq) & 1u)) hb = 0u;
+      const uint32_t c = __popc(hb);
+      const Cursor o = __shfl_sync(0xffffffffu, out, qq) + (Cursor)bef;
+      const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
+      const uint32_t sb = BATCH ? __shfl_sync(0xffffffffu, sub_base, qq) : 0u;
+      uint32_t incl = c;  // inclusive scan of the pair counts over the lanes
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          xs[u] = __shfl_sync(0xffffffffu, mine.x, j0 + u);
-          hs[u] = __shfl_sync(0xffffffffu, mine.y, j0 + u);  // 0 past the end
-          if (!all_valid && !((vmask >> (xs[u] & 31u)) & 1u)) hs[u] = 0u;
-          ss[u] = ((hs[u] >> lane) & 1u) ? t.sid[(xs[u] >> 5) * 32u + lane] : 0u;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          if (hs[u] == 0u) continue;
-          const int qq = (int)(xs[u] & 31u);
-          const Cursor o = __shfl_sync(0xffffffffu, out, qq);
-          const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
-          const uint32_t sb = BATCH ? __shfl_sync(0xffffffffu, sub_base, qq) : 0u;
-          if ((hs[u] >> lane) & 1u) {
+      for (int d2 = 1; d2 < 32; d2 <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d2);
+        if (lane >= d2) incl += y;
+      }
+      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+      const uint32_t excl = incl - c;
+      const uint32_t* sid_leaf = t.sid + (x >> 5) * 32u;
+      for (uint32_t base = 0; base < total; base += kReplayBuf) {
+        // stage: every lane writes its record's pairs that fall in this round
+        uint32_t m = hb, k = 0;
+        while (m) {
+          const uint32_t bit = __ffs(m) - 1u;
+          m &= m - 1u;
+          const uint32_t slot = excl + k - base;  // wraps for slots before base
+          if (slot < (uint32_t)kReplayBuf) {
             ddm_pair pr;
             pr.upd = Qq;
-            pr.sub = ss[u] - sb;
-            w.pairs[(unsigned long long)(o + (Cursor)__popc(hs[u] & lt))] = pr;
+            pr.sub = sid_leaf[bit] - sb;
+            s_pair[wib][slot] = pr;
+            s_pos[wib][slot] = o + (Cursor)k;
           }
-          if (lane == qq) out = o + (Cursor)__popc(hs[u]);
+          ++k;
         }
+        __syncwarp();
+        const uint32_t nround = min((uint32_t)kReplayBuf, total - base);
+        for (uint32_t tt = lane; tt < nround; tt += 32u)
+          w.pairs[(unsigned long long)s_pos[wib][tt]] = s_pair[wib][tt];
+        __syncwarp();
       }
     }
   }
@@ -539,7 +611,7 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView
   if (p1 <= p0) return cudaSuccess;
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
-  const uint32_t blocks = (uint32_t)sms * 6u;  // persistent: work = record blocks
+  const uint32_t blocks = (uint32_t)sms * 4u;  // persistent: work = record blocks
   // Cursors fit 32 bits when the range's pairs do; the capacity bounds them.
   const bool wide = w.capacity > 0xffffffffull;
   if (id_filter) {
