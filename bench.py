@@ -40,7 +40,7 @@ DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
 # DRAM bytes (read + write) per pair of the write-pass kernel (k_replay), from
 # the ncu capture summarised in profiles/k_replay_clustered_d3_scale0.15.md
 # (a smaller case of the same workload; traffic scales with pairs written).
-TRAFFIC_PER_PAIR = 10.25
+TRAFFIC_PER_PAIR = 9.96
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -307,6 +307,7 @@ def serving_section(seconds: float = 2.0, slots: int = 8):
     budget = int(free * 0.4)
     srv = S.Server(regions, l, slots=slots, budget_bytes=budget, pair_capacity=1 << 26)
     try:
+        srv.warm_up(1_000_000)
         t0 = time.perf_counter()
         done = srv.run(sched, mover=mover, step_s=0.010)
         wall = time.perf_counter() - t0
@@ -318,6 +319,7 @@ def serving_section(seconds: float = 2.0, slots: int = 8):
                              seed=r.seed) for r in sched[:plain_n]]
     one = S.Server(regions, l, slots=1, budget_bytes=budget, pair_capacity=1 << 26)
     try:
+        one.warm_up(1_000_000)
         t0 = time.perf_counter()
         pdone = one.run(plain_sched, mover=None)
         plain_wall = time.perf_counter() - t0

@@ -186,6 +186,22 @@ int ddm_write(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end,
 int ddm_chunk_end(ddm_ctx *ctx, uint32_t upd_begin, uint64_t capacity,
                   uint32_t *upd_end, void *stream);
 
+/* Host-synchronisation-free staged calls, for request loops that keep
+ * several contexts busy on their own streams.  ddm_plan_async enqueues what
+ * ddm_plan does (offsets stay inside the context) and returns at once;
+ * ddm_write_async enqueues what ddm_write does and then copies the number of
+ * pairs written to k_dev[0] and the device error bits to err_dev[0] (1 =
+ * invalid extent in the plan's updates, 2 = bounded wait timed out, 4 =
+ * more pairs than capacity, nothing written), both DEVICE pointers (either
+ * may be NULL; use pinned host memory to read them after a stream event).
+ * The calls allocate device memory only when sizes grow beyond earlier
+ * calls on the context.  Errors returned directly: DDM_ERR_ARG,
+ * DDM_ERR_STATE, DDM_ERR_NOMEM, DDM_ERR_CUDA. */
+int ddm_plan_async(ddm_ctx *ctx, const float *upd_lo, const float *upd_hi, uint32_t m,
+                   uint32_t flags, void *stream);
+int ddm_write_async(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end, ddm_pair *pairs,
+                    uint64_t capacity, uint64_t *k_dev, uint32_t *err_dev, void *stream);
+
 /* Plan order.  The counting pass runs the updates in a spatial order (the
  * same order as the tree, so that the 32 queries of a warp lie close
  * together).  Writing ranges of that order keeps every chunk's queries

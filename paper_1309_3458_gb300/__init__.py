@@ -52,6 +52,8 @@ SIGNATURES = {
     "ddm_build": (_i, [_vp, _i, _vp, _vp, _u32, _vp]),
     "ddm_plan": (_i, [_vp, _vp, _vp, _u32, _u32, _vp, _pu64, _vp]),
     "ddm_refit": (_i, [_vp, _vp, _vp, _vp]),
+    "ddm_plan_async": (_i, [_vp, _vp, _vp, _u32, _u32, _vp]),
+    "ddm_write_async": (_i, [_vp, _u32, _u32, _vp, _u64, _vp, _vp, _vp]),
     "ddm_attach": (_i, [_vp, _vp]),
     "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
@@ -199,6 +201,18 @@ def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
     rc = lib().ddm_plan(ctx, ul, uh, m, flags, _ptr(offsets), ctypes.byref(k), _stream(stream))
     _check(rc, "ddm_plan", k.value)
     return k.value
+
+
+def ddm_plan_async(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, stream=None) -> None:
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    _check(lib().ddm_plan_async(ctx, ul, uh, m, flags, _stream(stream)), "ddm_plan_async")
+
+
+def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, err_dev=None,
+                    stream=None) -> None:
+    cap = 0 if pairs is None else pairs.shape[0]
+    _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, _ptr(k_dev),
+                                 _ptr(err_dev), _stream(stream)), "ddm_write_async")
 
 
 def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int:

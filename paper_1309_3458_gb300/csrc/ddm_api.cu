@@ -600,6 +600,36 @@ int ddm_chunk_end(ddm_ctx* c, uint32_t begin, uint64_t capacity, uint32_t* upd_e
   return DDM_OK;
 }
 
+int ddm_plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_t flags,
+                   void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->built || c->bv.count) return DDM_ERR_STATE;
+  if (!set_ok(c->tree.d, ulo, uhi, m) || (flags & ~DDM_OPEN)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags, true, s));
+  return DDM_OK;
+}
+
+int ddm_write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
+                    uint64_t* k_dev, uint32_t* err_dev, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  if (begin > end || end > c->m || (end > begin && !pairs && capacity > 0)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // keep the plan's error bits; the write sets K (and the capacity bit)
+  DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
+  if (k_dev)
+    DDM_CUDA(cudaMemcpyAsync(k_dev, &c->st_dev->K, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
+  if (err_dev)
+    DDM_CUDA(cudaMemcpyAsync(err_dev, &c->st_dev->err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  return DDM_OK;
+}
+
 int ddm_write_ordered(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, ddm_pair* pairs,
                       uint64_t capacity, uint64_t* k_out, void* stream) {
   if (!c) return DDM_ERR_ARG;

@@ -19,7 +19,6 @@ torch generators (workload generation, not matching arithmetic).
 from __future__ import annotations
 
 import math
-import queue
 import threading
 import time
 from dataclasses import dataclass, field
@@ -141,7 +140,16 @@ def poisson_schedule(rate: float, duration: float, federates: int, size_lo: int,
 
 
 class Server:
-    """Continuous batching over `slots` contexts/streams with a byte budget."""
+    """Continuous batching over `slots` contexts, each with its own CUDA
+    stream, under a device-memory budget.
+
+    One dispatcher thread admits arrived requests into free slots (arrival
+    order, while the budget allows), enqueues each request's whole match with
+    the host-synchronisation-free calls (generation of its update set,
+    ``ddm_plan_async``, ``ddm_write_async``, an event), and polls the slots'
+    events; requests therefore overlap on the GPU without waiting for one
+    another.  A request pins the subscription version active when it is
+    admitted and releases it when its event completes."""
 
     def __init__(self, regions: ResidentRegions, l: float, slots: int = 8,
                  budget_bytes: Optional[int] = None, pair_capacity: int = 1 << 25,
@@ -153,20 +161,19 @@ class Server:
         free, _ = torch.cuda.mem_get_info()
         self.budget = budget_bytes if budget_bytes is not None else int(free * 0.5)
         self.reserved = 0
-        self.lock = threading.Lock()
         self.cap = pair_capacity
         self.slots = []
         for _ in range(slots):
-            ctx = ddm.ddm_create(torch.cuda.current_device())
-            s = torch.cuda.Stream()
-            buf = torch.empty((pair_capacity, 2), dtype=torch.int32, device="cuda")
-            inbox: "queue.Queue[Optional[Request]]" = queue.Queue()
-            self.slots.append({"ctx": ctx, "stream": s, "buf": buf, "inbox": inbox, "busy": False})
-        self.done: "queue.Queue[Request]" = queue.Queue()
-        self.threads = [threading.Thread(target=self._worker, args=(i,), daemon=True)
-                        for i in range(slots)]
-        for t in self.threads:
-            t.start()
+            self.slots.append({
+                "ctx": ddm.ddm_create(torch.cuda.current_device()),
+                "stream": torch.cuda.Stream(),
+                "buf": torch.empty((pair_capacity, 2), dtype=torch.int32, device="cuda"),
+                "kd": torch.zeros(1, dtype=torch.int64, device="cuda"),
+                "ed": torch.zeros(1, dtype=torch.int32, device="cuda"),
+                "kh": torch.zeros(1, dtype=torch.int64).pin_memory(),
+                "eh": torch.zeros(1, dtype=torch.int32).pin_memory(),
+                "event": torch.cuda.Event(),
+                "req": None, "ver": -1, "keep": None})
         self.t0 = 0.0
 
     def estimate(self, r: Request) -> int:
@@ -177,87 +184,136 @@ class Server:
         k = r.size * self.regions.n * p ** self.regions.d
         return int(r.size * (72 + 16 * self.regions.d) + 16 * k)
 
-    def _worker(self, i: int):
+    def _launch(self, slot, r: Request):
         import torch
-        slot = self.slots[i]
-        ctx, s, buf = slot["ctx"], slot["stream"], slot["buf"]
-        while True:
-            r = slot["inbox"].get()
-            if r is None:
-                return
-            v, step = self.regions.acquire()
-            try:
-                ddm.ddm_attach(ctx, self.regions.ctx[v])
-                with torch.cuda.stream(s):
-                    lo, hi = request_updates(r.seed, r.size, self.regions.d, self.l)
-                    r.K = ddm.ddm_plan(ctx, lo, hi, stream=s)
-                    parts = []
-                    b = 0
-                    while b < r.size:
-                        e = ddm.ddm_chunk_end_ordered(ctx, b, self.cap, stream=s)
-                        k = ddm.ddm_write_ordered(ctx, b, e, buf, stream=s)
-                        if self.keep_pairs:
-                            parts.append(buf[:k].cpu().numpy().view(np.uint32).copy())
-                        b = e
+        v, step = self.regions.acquire()
+        ctx, s = slot["ctx"], slot["stream"]
+        ddm.ddm_attach(ctx, self.regions.ctx[v])
+        with torch.cuda.stream(s):
+            lo, hi = request_updates(r.seed, r.size, self.regions.d, self.l)
+            ddm.ddm_plan_async(ctx, lo, hi, stream=s)
+            ddm.ddm_write_async(ctx, 0, r.size, slot["buf"], slot["kd"], slot["ed"], stream=s)
+            slot["kh"].copy_(slot["kd"], non_blocking=True)
+            slot["eh"].copy_(slot["ed"], non_blocking=True)
+            slot["event"].record(s)
+        slot["req"], slot["ver"], slot["keep"] = r, v, (lo, hi)
+        r.version, r.step = v, step
+
+    def _finish(self, slot):
+        import torch
+        r = slot["req"]
+        err = int(slot["eh"][0])
+        if err & 1:
+            raise ValueError(f"request {r.rid}: invalid extent")
+        if err & 4:  # more pairs than the slot buffer: stream them out in ordered chunks
+            ctx, s = slot["ctx"], slot["stream"]
+            with torch.cuda.stream(s):
+                lo, hi = slot["keep"]
+                r.K = ddm.ddm_plan(ctx, lo, hi, stream=s)
+                parts, b = [], 0
+                while b < r.size:
+                    e = ddm.ddm_chunk_end_ordered(ctx, b, self.cap, stream=s)
+                    k = ddm.ddm_write_ordered(ctx, b, e, slot["buf"], stream=s)
                     if self.keep_pairs:
-                        r.pairs = np.concatenate(parts) if parts else np.zeros((0, 2), np.uint32)
-                    s.synchronize()
-            finally:
-                self.regions.release(v)
-            r.version, r.step = v, step
-            r.done = time.perf_counter() - self.t0
-            with self.lock:
-                self.reserved -= r.est_bytes
-                slot["busy"] = False
-            self.done.put(r)
+                        parts.append(slot["buf"][:k].cpu().numpy().view(np.uint32).copy())
+                    b = e
+                if self.keep_pairs:
+                    r.pairs = np.concatenate(parts) if parts else np.zeros((0, 2), np.uint32)
+        else:
+            r.K = int(slot["kh"][0])
+            if self.keep_pairs:
+                with torch.cuda.stream(slot["stream"]):
+                    r.pairs = slot["buf"][:r.K].cpu().numpy().view(np.uint32).copy()
+        self.regions.release(slot["ver"])
+        r.done = time.perf_counter() - self.t0
+        self.reserved -= r.est_bytes
+        slot["req"], slot["keep"] = None, None
+
+    def warm_up(self, size: int):
+        """One request of `size` updates per slot, so that each slot's
+        workspace and record arena are sized before serving (the library
+        grows buffers with synchronous allocations)."""
+        for i, slot in enumerate(self.slots):
+            r = Request(rid=-1 - i, federate=0, arrival=0.0, size=size, seed=12345 + i)
+            self._launch(slot, r)
+        for slot in self.slots:
+            slot["event"].synchronize()
+            self._finish(slot)
+        # a second round, now that each context knows its record arena size
+        for i, slot in enumerate(self.slots):
+            self._launch(slot, Request(rid=-1 - i, federate=0, arrival=0.0, size=size,
+                                       seed=54321 + i))
+        for slot in self.slots:
+            slot["event"].synchronize()
+            self._finish(slot)
 
     def run(self, schedule: List[Request], mover=None, step_s: float = 0.010,
             timeout_s: float = 600.0) -> List[Request]:
         """Serve `schedule` in real time; `mover(step)` returns the regions'
-        coordinates after movement step `step` (called every step_s)."""
+        coordinates after movement step `step`; a separate thread applies a
+        step every step_s (refit of the idle version), so admissions never
+        wait for a refit."""
+        self.t0 = time.perf_counter()
+        stop = threading.Event()
+
+        def move():
+            import torch
+            step, next_step = 0, step_s
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                while not stop.is_set():
+                    now = time.perf_counter() - self.t0
+                    if now < next_step:
+                        time.sleep(min(0.001, next_step - now))
+                        continue
+                    step += 1
+                    lo, hi = mover(step)
+                    self.regions.step(lo, hi, step)
+                    next_step += step_s
+
+        mover_thread = threading.Thread(target=move, daemon=True) if mover is not None else None
+        if mover_thread:
+            mover_thread.start()
+        try:
+            return self._serve(schedule, timeout_s)
+        finally:
+            stop.set()
+            if mover_thread:
+                mover_thread.join()
+
+    def _serve(self, schedule, timeout_s):
         pending = list(schedule)
         waiting: List[Request] = []
         finished: List[Request] = []
-        self.t0 = time.perf_counter()
-        next_step, step = step_s, 0
         while len(finished) < len(schedule):
             now = time.perf_counter() - self.t0
             if now > timeout_s:
                 raise TimeoutError("serving run did not finish")
-            if mover is not None and now >= next_step:
-                step += 1
-                lo, hi = mover(step)
-                self.regions.step(lo, hi, step)
-                next_step += step_s
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.pop(0))
-            # admit in arrival order while a slot is free and the budget allows
-            while waiting:
+            for slot in self.slots:  # completions
+                if slot["req"] is not None and slot["event"].query():
+                    r = slot["req"]
+                    self._finish(slot)
+                    finished.append(r)
+            for slot in self.slots:  # admissions, in arrival order
+                if not waiting:
+                    break
+                if slot["req"] is not None:
+                    continue
                 r = waiting[0]
                 r.est_bytes = self.estimate(r)
-                with self.lock:
-                    free = [i for i, sl in enumerate(self.slots) if not sl["busy"]]
-                    fits = self.reserved + r.est_bytes <= self.budget or self.reserved == 0
-                    if not free or not fits:
-                        break
-                    self.reserved += r.est_bytes
-                    self.slots[free[0]]["busy"] = True
+                if self.reserved and self.reserved + r.est_bytes > self.budget:
+                    break
                 waiting.pop(0)
+                self.reserved += r.est_bytes
                 r.admitted = time.perf_counter() - self.t0
-                self.slots[free[0]]["inbox"].put(r)
-            try:
-                while True:
-                    finished.append(self.done.get_nowait())
-            except queue.Empty:
-                pass
-            time.sleep(0.0001)
+                self._launch(slot, r)
+            if all(sl["req"] is not None for sl in self.slots) or not waiting:
+                time.sleep(0.00005)
         return sorted(finished, key=lambda r: r.rid)
 
     def close(self):
-        for sl in self.slots:
-            sl["inbox"].put(None)
-        for t in self.threads:
-            t.join()
         for sl in self.slots:
             ddm.ddm_destroy(sl["ctx"])
 
