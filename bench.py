@@ -277,22 +277,31 @@ def batched_section(reps: int = 3):
         ddm.ddm_destroy(ctx)
 
 
-def serving_section(seconds: float = 2.0, slots: int = 8):
+def serving_section(seconds: float = 2.0, slots: int = 4, saturated_seconds: float = 1.0):
     """Serving: d = 2, 1e6 resident subscription regions (side 1e3, i.e.
     alpha = 1 at N = 1e6) moving every 10 ms by a Gaussian random walk
     (sigma = 1e-3 L, reflected); 64 federates send match requests with
     Poisson arrivals (2,000 per second in total) and update-set sizes
     log-uniform in [1e3, 1e6]; continuous batching over `slots` streams with
-    admission by a device-memory budget."""
+    admission by a device-memory budget.  The federates' update sets are on
+    the device when their requests arrive.
+
+    Three runs: the real-time schedule (latency percentiles), a saturated
+    schedule whose requests all wait at t = 0 (throughput), and the same
+    saturated requests served plainly -- one ddm_plan + ddm_write per
+    request, one after another."""
     import torch
 
+    import paper_1309_3458_gb300 as ddm
     from paper_1309_3458_gb300 import serving as S
     d, n, l = 2, 1_000_000, 1000.0
     g = torch.Generator(device="cuda")
     g.manual_seed(2026)
     lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
     hi = (lo + l).contiguous()
-    regions = S.ResidentRegions(lo, hi)
+    # regions move by about their own side per step: rebuilding (re-sorting)
+    # the idle version every step beats refitting an ageing order
+    regions = S.ResidentRegions(lo, hi, rebuild_every=1)
     state = {"lo": lo, "hi": hi}
     mg = torch.Generator(device="cuda")
     mg.manual_seed(7)
@@ -301,39 +310,74 @@ def serving_section(seconds: float = 2.0, slots: int = 8):
         state["lo"], state["hi"] = S.random_walk(state["lo"], state["hi"], 1000.0, mg)
         return state["lo"], state["hi"]
 
+    def materialise(reqs):
+        sets = [S.request_updates(r.seed, r.size, d, l) for r in reqs]
+        torch.cuda.synchronize()
+        return sets
+
+    def attach(reqs, sets):
+        for r, (a, b) in zip(reqs, sets):
+            r.lo, r.hi = a, b
+
     sched = S.poisson_schedule(rate=2000.0, duration=seconds, federates=64, size_lo=1000,
                                size_hi=1_000_000, seed=1)
+    sat = S.poisson_schedule(rate=2000.0, duration=saturated_seconds, federates=64,
+                             size_lo=1000, size_hi=1_000_000, seed=2)
+    for r in sat:
+        r.arrival = 0.0
+    sched_sets, sat_sets = materialise(sched), materialise(sat)
     free, _ = torch.cuda.mem_get_info()
     budget = int(free * 0.4)
     srv = S.Server(regions, l, slots=slots, budget_bytes=budget, pair_capacity=1 << 26)
     try:
-        srv.warm_up(1_000_000)
+        srv.warm_up()
+        attach(sched, sched_sets)
         t0 = time.perf_counter()
         done = srv.run(sched, mover=mover, step_s=0.010)
         wall = time.perf_counter() - t0
+        rt_launches = srv.launches
+        attach(sat, sat_sets)
+        srv.launches = 0
+        t0 = time.perf_counter()
+        sdone = srv.run(sat, mover=None)     # fixed version: plain must find the same pairs
+        sat_wall = time.perf_counter() - t0
+        sat_launches = srv.launches
     finally:
         srv.close()
-    # plain: the first requests one after another on one context, no overlap
-    plain_n = min(len(sched), 400)
-    plain_sched = [S.Request(rid=r.rid, federate=r.federate, arrival=0.0, size=r.size,
-                             seed=r.seed) for r in sched[:plain_n]]
-    one = S.Server(regions, l, slots=1, budget_bytes=budget, pair_capacity=1 << 26)
+    # plain: one ddm_plan + ddm_write per request, one after another
+    ctx = ddm.ddm_create(torch.cuda.current_device())
+    buf = torch.empty((1 << 26, 2), dtype=torch.int32, device="cuda")
     try:
-        one.warm_up(1_000_000)
+        ddm.ddm_attach(ctx, regions.ctx[regions.active])
+        for a, b in sat_sets[:3]:     # warm-up: size the context's workspace
+            ddm.ddm_plan(ctx, a, b)
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
-        pdone = one.run(plain_sched, mover=None)
+        plain_K = 0
+        for r, (a, b) in zip(sat, sat_sets):
+            k = ddm.ddm_plan(ctx, a, b)
+            ddm.ddm_write(ctx, 0, r.size, buf)
+            plain_K += k
+        torch.cuda.synchronize()
         plain_wall = time.perf_counter() - t0
     finally:
-        one.close()
+        ddm.ddm_destroy(ctx)
         regions.close()
     out = S.summary(done, wall)
-    plain_q = sum(r.size for r in pdone) / plain_wall
-    out["plain_one_at_a_time"] = {"requests": plain_n, "wall_s": plain_wall,
-                                  "queries_per_s": plain_q,
-                                  "pairs_per_s": sum(r.K for r in pdone) / plain_wall}
-    out["served_over_plain"] = out["queries_per_s"] / plain_q
+    out["launches"] = rt_launches
+    sq = sum(r.size for r in sdone)
+    sK = sum(r.K for r in sdone)
+    out["saturated"] = {"requests": len(sdone), "wall_s": sat_wall, "launches": sat_launches,
+                        "queries_per_s": sq / sat_wall, "pairs_per_s": sK / sat_wall,
+                        "p50_ms": S.summary(sdone, sat_wall)["p50_ms"]}
+    out["plain_one_at_a_time"] = {"requests": len(sat), "wall_s": plain_wall,
+                                  "queries_per_s": sq / plain_wall,
+                                  "pairs_per_s": plain_K / plain_wall,
+                                  "same_pairs": plain_K == sK}
+    out["served_over_plain"] = plain_wall / sat_wall
     out.update({"workload": "d=2, 1e6 moving regions, 64 federates, 2000 req/s Poisson, "
                             "sizes log-uniform [1e3, 1e6]",
+                "rebuilds": regions.rebuilds, "refits": regions.refits,
                 "slots": slots, "budget_gb": budget / 1e9, "offered_s": seconds,
                 "steps": max(r.step for r in done) if done else 0})
     return out

@@ -202,6 +202,20 @@ int ddm_plan_async(ddm_ctx *ctx, const float *upd_lo, const float *upd_hi, uint3
 int ddm_write_async(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end, ddm_pair *pairs,
                     uint64_t capacity, uint64_t *k_dev, uint32_t *err_dev, void *stream);
 
+/* Output offsets of update-id boundaries, for one plan that matches several
+ * update sets at once (concatenated, set r holding update ids
+ * [upd_off[r], upd_off[r+1])): pair_off[i] = number of pairs of the updates
+ * with id < upd_off[i], 0 <= i <= count, i.e. set r's pairs are
+ * [pair_off[r], pair_off[r+1]) of the output of ddm_write(0, m) (pairs by
+ * update id, Section IV's per-query result lists one after another).
+ *  upd_off[count+1]  (DEVICE, uint64) non-decreasing update ids; entries
+ *                    above m are read as m;
+ *  pair_off[count+1] (DEVICE, uint64) output.
+ * Enqueued on `stream` after the plan; no synchronisation, no allocation.
+ * DDM_ERR_ARG for NULL pointers, DDM_ERR_STATE without a plan. */
+int ddm_pair_offsets_async(ddm_ctx *ctx, const uint64_t *upd_off, uint32_t count,
+                           uint64_t *pair_off, void *stream);
+
 /* Plan order.  The counting pass runs the updates in a spatial order (the
  * same order as the tree, so that the 32 queries of a warp lie close
  * together).  Writing ranges of that order keeps every chunk's queries

@@ -54,6 +54,7 @@ SIGNATURES = {
     "ddm_refit": (_i, [_vp, _vp, _vp, _vp]),
     "ddm_plan_async": (_i, [_vp, _vp, _vp, _u32, _u32, _vp]),
     "ddm_write_async": (_i, [_vp, _u32, _u32, _vp, _u64, _vp, _vp, _vp]),
+    "ddm_pair_offsets_async": (_i, [_vp, _vp, _u32, _vp, _vp]),
     "ddm_attach": (_i, [_vp, _vp]),
     "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
@@ -213,6 +214,16 @@ def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, e
     cap = 0 if pairs is None else pairs.shape[0]
     _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, _ptr(k_dev),
                                  _ptr(err_dev), _stream(stream)), "ddm_write_async")
+
+
+def ddm_pair_offsets_async(ctx: int, upd_off, pair_off, stream=None) -> None:
+    """pair_off[i] = pairs of the updates with id < upd_off[i] in the current
+    plan (both uint64/int64 device tensors of count + 1 entries)."""
+    count = upd_off.shape[0] - 1
+    if count < 0 or pair_off.shape[0] < count + 1:
+        raise ValueError("upd_off and pair_off need count + 1 entries")
+    _check(lib().ddm_pair_offsets_async(ctx, _ptr(upd_off), count, _ptr(pair_off), _stream(stream)),
+           "ddm_pair_offsets_async")
 
 
 def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int:

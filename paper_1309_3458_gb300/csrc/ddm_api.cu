@@ -46,7 +46,10 @@ struct ddm_ctx {
       blk_counter;
   uint64_t replay_budget = 0;   // bytes; 0 = never record
   uint32_t rec_blocks = 0;      // blocks of the current arena
-  uint32_t rec_hint = 0;        // blocks the last count pass asked for
+  // Blocks and packets of the latest recorded count pass, copied back by
+  // every plan without a host synchronisation (pinned; read as a sizing hint
+  // for the next arena, possibly one plan stale).
+  volatile uint32_t* rec_hint = nullptr;
   RecordArena arena{};          // arena of the current plan (max_blocks 0 = none)
   // batched instances
   DevBuf inst_s, inst_u, bglog2, bngroups, bgbase;
@@ -321,7 +324,12 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
     const uint32_t packets = (m + 31) / 32;
     // bytes per block: records (three words each), next/count/packet/list entries
     const uint64_t per_block = (uint64_t)kRecBlock * 3 * sizeof(uint32_t) + 4 * sizeof(uint32_t);
-    uint64_t want = c->rec_hint ? (uint64_t)c->rec_hint + c->rec_hint / 8 + 64 : 2ull * packets;
+    const uint32_t hint_blocks = c->rec_hint[0], hint_packets = c->rec_hint[1];
+    uint64_t want = 2ull * packets;
+    if (hint_packets) {  // blocks per packet of the last pass, plus 1/8 and some slack
+      const double per_packet = (double)hint_blocks / (double)hint_packets;
+      want = (uint64_t)(per_packet * 1.125 * (double)packets) + 64;
+    }
     const uint64_t cap_blocks = c->replay_budget / per_block;
     if (want > cap_blocks) want = cap_blocks;
     if (want > 0xfffffff0ull) want = 0xfffffff0ull;
@@ -333,7 +341,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
         ensure(c, c->pkt_first, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_nblk, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_off, ((size_t)packets + 1) * sizeof(unsigned long long)) == DDM_OK &&
-        ensure(c, c->blk_counter, 2 * sizeof(uint32_t)) == DDM_OK) {
+        ensure(c, c->blk_counter, 3 * sizeof(uint32_t)) == DDM_OK) {
       c->arena.rec = static_cast<uint32_t*>(c->rec.p);
       c->arena.blk_next = static_cast<uint32_t*>(c->blk_next.p);
       c->arena.blk_count = static_cast<uint32_t*>(c->blk_count.p);
@@ -344,7 +352,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
       c->arena.pkt_off = static_cast<unsigned long long*>(c->pkt_off.p);
       c->arena.blk_counter = static_cast<uint32_t*>(c->blk_counter.p);
       c->arena.max_blocks = (uint32_t)want;
-      DDM_CUDA(cudaMemsetAsync(c->blk_counter.p, 0, 2 * sizeof(uint32_t), s));
+      DDM_CUDA(cudaMemsetAsync(c->blk_counter.p, 0, 3 * sizeof(uint32_t), s));
     }
   }
   if (m > 0) {
@@ -372,9 +380,9 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
     DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets, c->arena.pkt_off, sums, nullptr, s));
     DDM_CUDA(launch_block_list(c->arena, packets, s));
   }
-  if (c->arena.max_blocks)  // blocks the count pass asked for, read back with the status
-    DDM_CUDA(cudaMemcpyAsync(&c->st_dev->aux, static_cast<uint32_t*>(c->blk_counter.p) + 1,
-                             sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
+  if (c->arena.max_blocks)  // blocks needed and packets, the next arena's sizing hint
+    DDM_CUDA(cudaMemcpyAsync((void*)c->rec_hint, static_cast<uint32_t*>(c->blk_counter.p) + 1,
+                             2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   c->ulo = ulo;
   c->uhi = uhi;
   c->flags = flags;
@@ -485,11 +493,13 @@ int ddm_create(ddm_ctx** out, int device) {
   }
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&c->st_dev, sizeof(Status)) != cudaSuccess ||
-      cudaMallocHost(&c->st_host, sizeof(Status)) != cudaSuccess) {
+      cudaMallocHost(&c->st_host, sizeof(Status)) != cudaSuccess ||
+      cudaMallocHost((void**)&c->rec_hint, 2 * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     ddm_destroy(c);
     return DDM_ERR_NOMEM;
   }
+  c->rec_hint[0] = c->rec_hint[1] = 0;
   *out = c;
   return DDM_OK;
 }
@@ -508,6 +518,7 @@ int ddm_destroy(ddm_ctx* c) {
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
+  if (c->rec_hint) cudaFreeHost((void*)c->rec_hint);
   delete c;
   return DDM_OK;
 }
@@ -515,7 +526,6 @@ int ddm_destroy(ddm_ctx* c) {
 int ddm_set_replay_budget(ddm_ctx* c, uint64_t bytes) {
   if (!c) return DDM_ERR_ARG;
   c->replay_budget = bytes;
-  c->rec_hint = 0;
   return DDM_OK;
 }
 
@@ -563,7 +573,6 @@ int ddm_plan(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_
     DDM_CUDA(cudaMemcpyAsync(offsets, c->offsets.p, sizeof(unsigned long long) * ((size_t)m + 1),
                              cudaMemcpyDeviceToDevice, s));
   DDM_TRY(sync_status(c, s));
-  if (c->arena.max_blocks) c->rec_hint = (uint32_t)c->st_host->aux;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   if (rc != DDM_OK) c->planned = false;
@@ -630,6 +639,19 @@ int ddm_write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, u
   return DDM_OK;
 }
 
+int ddm_pair_offsets_async(ddm_ctx* c, const uint64_t* upd_off, uint32_t count, uint64_t* pair_off,
+                           void* stream) {
+  if (!c || !upd_off || !pair_off) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  DDM_CUDA(launch_gather_offsets(static_cast<const unsigned long long*>(c->offsets.p), c->m,
+                                 reinterpret_cast<const unsigned long long*>(upd_off), count,
+                                 reinterpret_cast<unsigned long long*>(pair_off),
+                                 static_cast<cudaStream_t>(stream)));
+  return DDM_OK;
+}
+
 int ddm_write_ordered(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, ddm_pair* pairs,
                       uint64_t capacity, uint64_t* k_out, void* stream) {
   if (!c) return DDM_ERR_ARG;
@@ -693,11 +715,7 @@ static int match_impl(ddm_ctx* c, int d, const float* ulo, const float* uhi, uin
     if (end > begin && !pairs && capacity > 0) return DDM_ERR_ARG;
     DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
   }
-  if (c->arena.max_blocks)
-    DDM_CUDA(cudaMemcpyAsync(&c->st_dev->aux, static_cast<uint32_t*>(c->blk_counter.p) + 1,
-                             sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   DDM_TRY(sync_status(c, s));
-  if (c->arena.max_blocks) c->rec_hint = (uint32_t)c->st_host->aux;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   if (rc == DDM_ERR_EXTENT || rc == DDM_ERR_TIMEOUT) c->built = c->planned = false;
@@ -750,13 +768,10 @@ static int batch_impl(ddm_ctx* c, int d, uint32_t count, const float* ulo, const
   DDM_TRY(plan_async(c, ulo, uhi, m, flags, true, s, &bs_u));
   DDM_TRY(write_async(c, 0, m, pairs, capacity, s));
   if (pair_off && m > 0)
-    DDM_CUDA(launch_gather_offsets(static_cast<const unsigned long long*>(c->offsets.p), uoff,
+    DDM_CUDA(launch_gather_offsets(static_cast<const unsigned long long*>(c->offsets.p), m, uoff,
                                    count, reinterpret_cast<unsigned long long*>(pair_off), s));
   else if (pair_off)
     DDM_CUDA(cudaMemsetAsync(pair_off, 0, sizeof(uint64_t) * ((size_t)count + 1), s));
-  if (c->arena.max_blocks)
-    DDM_CUDA(cudaMemcpyAsync(&c->st_dev->aux, static_cast<uint32_t*>(c->blk_counter.p) + 1,
-                             sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   if (k_dev)
     DDM_CUDA(cudaMemcpyAsync(k_dev, &c->st_dev->K, sizeof(uint64_t), cudaMemcpyDeviceToDevice, s));
   if (err_dev)
@@ -765,7 +780,6 @@ static int batch_impl(ddm_ctx* c, int d, uint32_t count, const float* ulo, const
   c->built = c->planned = false;
   if (!sync) return DDM_OK;
   DDM_TRY(sync_status(c, s));
-  if (c->arena.max_blocks) c->rec_hint = (uint32_t)c->st_host->aux;
   if (k_out) *k_out = c->st_host->K;
   return status_code(*c->st_host);
 }

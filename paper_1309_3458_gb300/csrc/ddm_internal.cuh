@@ -189,7 +189,7 @@ struct RecordArena {
   unsigned long long* pkt_off;  // [packets + 1] exclusive prefix of pkt_nblk
   uint32_t* blk_list;      // [max_blocks] blocks in plan order
   uint32_t* blk_counter;   // [0] blocks handed out (may exceed max_blocks),
-                           // [1] blocks the whole pass needed
+                           // [1] blocks the whole pass needed, [2] packets
   uint32_t max_blocks;     // 0: no recording
 };
 // The records of the last count pass are complete (the write pass may
@@ -221,8 +221,8 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView
                           const RecordArena& ra, const WriteView& w, uint32_t p0, uint32_t p1,
                           uint32_t pb, uint32_t pe, bool id_filter, uint32_t idb, uint32_t ide,
                           uint32_t* work, Status* st, int sms, cudaStream_t s);
-// pair_off[i] = offsets[upd_off[i]] for i <= count.
-cudaError_t launch_gather_offsets(const unsigned long long* offsets,
+// pair_off[i] = offsets[min(upd_off[i], m)] for i <= count.
+cudaError_t launch_gather_offsets(const unsigned long long* offsets, uint32_t m,
                                   const unsigned long long* upd_off, uint32_t count,
                                   unsigned long long* pair_off, cudaStream_t s);
 

@@ -397,6 +397,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
 
 // Plan-order list of record blocks: one thread per packet copies its chain.
 __global__ void k_block_list(RecordArena ra, uint32_t packets) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) ra.blk_counter[2] = packets;  // sizing hint
   if (!records_complete(ra)) return;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < packets;
        p += gridDim.x * blockDim.x) {
@@ -573,11 +574,13 @@ void dispatch_replay(bool wide, uint32_t blocks, cudaStream_t s, const TreeView&
                                                                   idb, ide, work, st);
 }
 
-__global__ void k_gather_offsets(const unsigned long long* __restrict__ offsets,
+__global__ void k_gather_offsets(const unsigned long long* __restrict__ offsets, uint32_t m,
                                  const unsigned long long* __restrict__ upd_off, uint32_t count,
                                  unsigned long long* __restrict__ pair_off) {
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += gridDim.x * blockDim.x)
-    pair_off[i] = offsets[upd_off[i]];
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i <= count; i += gridDim.x * blockDim.x) {
+    const unsigned long long u = upd_off[i];
+    pair_off[i] = offsets[u < m ? u : m];
+  }
 }
 
 }  // namespace
@@ -629,11 +632,11 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView
   return cudaGetLastError();
 }
 
-cudaError_t launch_gather_offsets(const unsigned long long* offsets,
+cudaError_t launch_gather_offsets(const unsigned long long* offsets, uint32_t m,
                                   const unsigned long long* upd_off, uint32_t count,
                                   unsigned long long* pair_off, cudaStream_t s) {
   const uint32_t blocks = (count + 256) / 256 < 1024 ? (count + 256) / 256 : 1024;
-  k_gather_offsets<<<blocks, 256, 0, s>>>(offsets, upd_off, count, pair_off);
+  k_gather_offsets<<<blocks, 256, 0, s>>>(offsets, m, upd_off, count, pair_off);
   note_launches(1);
   return cudaGetLastError();
 }

@@ -6,11 +6,15 @@ extents move, and each update set queries the subscription tree again.  Here
 the subscriptions stay resident on the device in two tree versions; every
 movement step refits the idle version in place (``ddm_refit``: same order,
 new per-node bounds) and makes it the active one.  Match requests (update
-sets of any size) arrive over time; each is admitted to a free slot when the
-memory budget allows, pins the version active at admission, and runs on the
-slot's own CUDA stream and context (``ddm_attach``), so requests admitted
-while others run overlap on the GPU.  A version is refitted only when no
-request pins it, so a request's result does not depend on what else runs.
+sets of any size) arrive over time; whenever a slot (context, stream,
+buffers) is free, the waiting requests that fit its limits and the memory
+budget are admitted together, matched against the version active at
+admission in one plan and one write pass over their concatenated update
+sets, and pin that version until they complete.  Slots run concurrently, so
+requests admitted while others run overlap on the GPU.  A version is refitted
+only when no request pins it, and the queries of one update set are
+independent of the others in the launch (Section IV), so a request's result
+does not depend on what else runs.
 
 Host orchestration only: every step of the matching runs in libddm's
 kernels.  Update sets and movement are synthesised on the device with seeded
@@ -22,7 +26,7 @@ import math
 import threading
 import time
 from dataclasses import dataclass, field
-from typing import Dict, List, Optional
+from typing import Any, Dict, List, Optional
 
 import numpy as np
 
@@ -56,9 +60,17 @@ def random_walk(lo, hi, sigma: float, gen):
 
 
 class ResidentRegions:
-    """Subscriptions kept on the device in two tree versions."""
+    """Subscriptions kept on the device in two tree versions.
 
-    def __init__(self, lo, hi, keep_history: bool = False):
+    A movement step brings the idle version up to date and activates it,
+    by an in-place refit (same order, new node bounds) or, every
+    `rebuild_every`-th step, by a full rebuild (re-sort).  A refit keeps the
+    result exact, but the order ages: the regions of a leaf drift apart, its
+    bounding box grows and the queries test more candidates, so the order is
+    renewed periodically (`rebuild_every` = 0: refit only; 1: rebuild every
+    step)."""
+
+    def __init__(self, lo, hi, keep_history: bool = False, rebuild_every: int = 1):
         import torch
         self.d, self.n = lo.shape
         self.ctx = [ddm.ddm_create(lo.device.index or 0) for _ in range(2)]
@@ -72,6 +84,8 @@ class ResidentRegions:
         self.refs = [0, 0]
         self.cv = threading.Condition()
         self.history = {0: (lo.clone(), hi.clone())} if keep_history else None
+        self.rebuild_every = rebuild_every
+        self.rebuilds = self.refits = 0
 
     def acquire(self):
         with self.cv:
@@ -85,7 +99,8 @@ class ResidentRegions:
             self.cv.notify_all()
 
     def step(self, lo, hi, step_index: int):
-        """Refit the idle version to the new coordinates and activate it."""
+        """Bring the idle version to the new coordinates (refit or rebuild)
+        and activate it."""
         import torch
         with self.cv:
             idle = 1 - self.active
@@ -95,8 +110,14 @@ class ResidentRegions:
             with torch.cuda.stream(self.stream):
                 self.pos[idle][0].copy_(lo)
                 self.pos[idle][1].copy_(hi)
-                ddm.ddm_refit(self.ctx[idle], self.pos[idle][0], self.pos[idle][1],
-                              stream=self.stream)
+                if self.rebuild_every and step_index % self.rebuild_every == 0:
+                    ddm.ddm_build(self.ctx[idle], self.pos[idle][0], self.pos[idle][1],
+                                  stream=self.stream)
+                    self.rebuilds += 1
+                else:
+                    ddm.ddm_refit(self.ctx[idle], self.pos[idle][0], self.pos[idle][1],
+                                  stream=self.stream)
+                    self.refits += 1
             self.step_of[idle] = step_index
             self.active = idle
             if self.history is not None:
@@ -121,6 +142,11 @@ class Request:
     step: int = -1
     K: int = 0
     pairs: Optional[np.ndarray] = None
+    lo: Any = None          # update set already on the device, (d, size); None: drawn
+    hi: Any = None          # from `seed` when the request is admitted
+    batch: int = -1         # launch the request ran in
+    base: int = 0           # its first update id within that launch
+    est_pairs: float = 0.0
 
 
 def poisson_schedule(rate: float, duration: float, federates: int, size_lo: int, size_hi: int,
@@ -140,19 +166,29 @@ def poisson_schedule(rate: float, duration: float, federates: int, size_lo: int,
 
 
 class Server:
-    """Continuous batching over `slots` contexts, each with its own CUDA
-    stream, under a device-memory budget.
+    """Continuous batching of match requests under a device-memory budget.
 
-    One dispatcher thread admits arrived requests into free slots (arrival
-    order, while the budget allows), enqueues each request's whole match with
-    the host-synchronisation-free calls (generation of its update set,
-    ``ddm_plan_async``, ``ddm_write_async``, an event), and polls the slots'
-    events; requests therefore overlap on the GPU without waiting for one
-    another.  A request pins the subscription version active when it is
-    admitted and releases it when its event completes."""
+    One dispatcher thread admits arrived requests in arrival order.  Whenever
+    one of the `slots` (a context, a CUDA stream, staging and pair buffers)
+    is free, every waiting request that fits the slot's limits and the memory
+    budget is admitted into it at once: their update sets are concatenated
+    and matched against the resident tree in ONE plan and ONE write pass
+    (``ddm_plan_async`` / ``ddm_write_async``, no host synchronisation), and
+    ``ddm_pair_offsets_async`` locates each request's pairs in the output,
+    which is laid out by update id.  The launch pins the subscription version
+    active at admission.  Slots run concurrently on their own streams; the
+    dispatcher polls their events, so requests that arrive while others are
+    on the GPU join the next free slot without waiting for them.  Under light
+    load a launch holds one request (low latency); under heavy load launches
+    grow (throughput).
 
-    def __init__(self, regions: ResidentRegions, l: float, slots: int = 8,
+    A request's pairs carry update ids relative to its own set: the pairs of
+    a launch hold ids within the launch, and request r's slice is shifted by
+    its base id ``r.base`` (done when ``keep_pairs`` copies them out)."""
+
+    def __init__(self, regions: ResidentRegions, l: float, slots: int = 4,
                  budget_bytes: Optional[int] = None, pair_capacity: int = 1 << 25,
+                 max_batch_updates: int = 1 << 24, max_batch_requests: int = 1024,
                  keep_pairs: bool = False):
         import torch
         self.regions = regions
@@ -162,90 +198,142 @@ class Server:
         self.budget = budget_bytes if budget_bytes is not None else int(free * 0.5)
         self.reserved = 0
         self.cap = pair_capacity
+        self.max_updates = max_batch_updates
+        self.max_requests = max_batch_requests
+        d = regions.d
         self.slots = []
         for _ in range(slots):
             self.slots.append({
                 "ctx": ddm.ddm_create(torch.cuda.current_device()),
                 "stream": torch.cuda.Stream(),
+                "lo": torch.empty(d * max_batch_updates, dtype=torch.float32, device="cuda"),
+                "hi": torch.empty(d * max_batch_updates, dtype=torch.float32, device="cuda"),
                 "buf": torch.empty((pair_capacity, 2), dtype=torch.int32, device="cuda"),
+                "uoff_h": torch.zeros(max_batch_requests + 1, dtype=torch.int64).pin_memory(),
+                "uoff_d": torch.zeros(max_batch_requests + 1, dtype=torch.int64, device="cuda"),
+                "poff_d": torch.zeros(max_batch_requests + 1, dtype=torch.int64, device="cuda"),
+                "poff_h": torch.zeros(max_batch_requests + 1, dtype=torch.int64).pin_memory(),
                 "kd": torch.zeros(1, dtype=torch.int64, device="cuda"),
                 "ed": torch.zeros(1, dtype=torch.int32, device="cuda"),
                 "kh": torch.zeros(1, dtype=torch.int64).pin_memory(),
                 "eh": torch.zeros(1, dtype=torch.int32).pin_memory(),
                 "event": torch.cuda.Event(),
-                "req": None, "ver": -1, "keep": None})
+                "batch": None, "ver": -1, "sets": None})
         self.t0 = 0.0
+        self.launches = 0
 
-    def estimate(self, r: Request) -> int:
-        # workspace of one plan (sort, sorted copy, counts, offsets, records)
-        # plus the expected pairs: E[K] = m * n * p^d, p = 2l/W - (l/W)^2
+    def expected_pairs(self, r: Request) -> float:
+        # uniform placement: per dimension an update overlaps a region with
+        # probability p = 2l/W - (l/W)^2 (W = L - l); E[K] = size * n * p^d
         W = L - self.l
         p = 2 * self.l / W - (self.l / W) ** 2
-        k = r.size * self.regions.n * p ** self.regions.d
-        return int(r.size * (72 + 16 * self.regions.d) + 16 * k)
+        return r.size * self.regions.n * p ** self.regions.d
 
-    def _launch(self, slot, r: Request):
+    def estimate(self, r: Request) -> int:
+        """Device bytes a request occupies while it runs: its share of a
+        plan's workspace (sort, sorted copy, counts, offsets, records) and of
+        the pair buffer."""
+        r.est_pairs = self.expected_pairs(r)
+        return int(r.size * (72 + 16 * self.regions.d) + 16 * r.est_pairs)
+
+    def _launch(self, slot, batch: List[Request]):
         import torch
         v, step = self.regions.acquire()
-        ctx, s = slot["ctx"], slot["stream"]
+        ctx, s, d = slot["ctx"], slot["stream"], self.regions.d
         ddm.ddm_attach(ctx, self.regions.ctx[v])
+        sizes = np.array([r.size for r in batch], dtype=np.int64)
+        offs = np.concatenate([[0], np.cumsum(sizes)])
+        M, count = int(offs[-1]), len(batch)
         with torch.cuda.stream(s):
-            lo, hi = request_updates(r.seed, r.size, self.regions.d, self.l)
+            for r in batch:
+                if r.lo is None:
+                    r.lo, r.hi = request_updates(r.seed, r.size, d, self.l)
+            if count == 1:
+                lo, hi = batch[0].lo, batch[0].hi
+            else:
+                lo = slot["lo"][:d * M].view(d, M)
+                hi = slot["hi"][:d * M].view(d, M)
+                torch.cat([r.lo for r in batch], dim=1, out=lo)
+                torch.cat([r.hi for r in batch], dim=1, out=hi)
+            slot["uoff_h"][:count + 1].numpy()[:] = offs
+            uoff = slot["uoff_d"][:count + 1]
+            poff = slot["poff_d"][:count + 1]
+            uoff.copy_(slot["uoff_h"][:count + 1], non_blocking=True)
             ddm.ddm_plan_async(ctx, lo, hi, stream=s)
-            ddm.ddm_write_async(ctx, 0, r.size, slot["buf"], slot["kd"], slot["ed"], stream=s)
+            ddm.ddm_write_async(ctx, 0, M, slot["buf"], slot["kd"], slot["ed"], stream=s)
+            ddm.ddm_pair_offsets_async(ctx, uoff, poff, stream=s)
             slot["kh"].copy_(slot["kd"], non_blocking=True)
             slot["eh"].copy_(slot["ed"], non_blocking=True)
+            slot["poff_h"][:count + 1].copy_(poff, non_blocking=True)
             slot["event"].record(s)
-        slot["req"], slot["ver"], slot["keep"] = r, v, (lo, hi)
-        r.version, r.step = v, step
+        for i, r in enumerate(batch):
+            r.version, r.step, r.batch, r.base = v, step, self.launches, int(offs[i])
+        self.launches += 1
+        slot["batch"], slot["ver"], slot["sets"] = batch, v, (lo, hi)
+
+    def _alone(self, slot, r: Request):
+        """One request by itself, its pairs streamed out in ordered chunks of
+        the slot buffer (used when a launch's pairs overflow the buffer)."""
+        import torch
+        ctx, s = slot["ctx"], slot["stream"]
+        with torch.cuda.stream(s):
+            r.K = ddm.ddm_plan(ctx, r.lo, r.hi, stream=s)
+            parts, b = [], 0
+            while b < r.size:
+                e = ddm.ddm_chunk_end_ordered(ctx, b, self.cap, stream=s)
+                k = ddm.ddm_write_ordered(ctx, b, e, slot["buf"], stream=s)
+                if self.keep_pairs:
+                    parts.append(slot["buf"][:k].cpu().numpy().view(np.uint32).copy())
+                b = e
+        if self.keep_pairs:
+            r.pairs = np.concatenate(parts) if parts else np.zeros((0, 2), np.uint32)
+        r.base = 0
 
     def _finish(self, slot):
-        import torch
-        r = slot["req"]
+        batch = slot["batch"]
         err = int(slot["eh"][0])
-        if err & 1:
-            raise ValueError(f"request {r.rid}: invalid extent")
-        if err & 4:  # more pairs than the slot buffer: stream them out in ordered chunks
-            ctx, s = slot["ctx"], slot["stream"]
-            with torch.cuda.stream(s):
-                lo, hi = slot["keep"]
-                r.K = ddm.ddm_plan(ctx, lo, hi, stream=s)
-                parts, b = [], 0
-                while b < r.size:
-                    e = ddm.ddm_chunk_end_ordered(ctx, b, self.cap, stream=s)
-                    k = ddm.ddm_write_ordered(ctx, b, e, slot["buf"], stream=s)
-                    if self.keep_pairs:
-                        parts.append(slot["buf"][:k].cpu().numpy().view(np.uint32).copy())
-                    b = e
-                if self.keep_pairs:
-                    r.pairs = np.concatenate(parts) if parts else np.zeros((0, 2), np.uint32)
+        if err & 3:
+            raise RuntimeError(f"launch of requests {[r.rid for r in batch]}: device error bits {err}")
+        if err & 4:  # more pairs than the slot buffer: each request alone, chunked
+            for r in batch:
+                self._alone(slot, r)
         else:
-            r.K = int(slot["kh"][0])
-            if self.keep_pairs:
-                with torch.cuda.stream(slot["stream"]):
-                    r.pairs = slot["buf"][:r.K].cpu().numpy().view(np.uint32).copy()
+            poff = slot["poff_h"][:len(batch) + 1].numpy().copy()
+            host = None
+            if self.keep_pairs and int(poff[-1]):
+                host = slot["buf"][:int(poff[-1])].cpu().numpy().view(np.uint32)
+            for i, r in enumerate(batch):
+                r.K = int(poff[i + 1] - poff[i])
+                if self.keep_pairs:
+                    pr = (host[poff[i]:poff[i + 1]].copy() if host is not None
+                          else np.zeros((0, 2), np.uint32))
+                    pr[:, 0] -= np.uint32(r.base)
+                    r.pairs = pr
         self.regions.release(slot["ver"])
-        r.done = time.perf_counter() - self.t0
-        self.reserved -= r.est_bytes
-        slot["req"], slot["keep"] = None, None
+        now = time.perf_counter() - self.t0
+        for r in batch:
+            r.done = now
+            self.reserved -= r.est_bytes
+            r.lo = r.hi = None
+        slot["batch"], slot["sets"] = None, None
 
-    def warm_up(self, size: int):
-        """One request of `size` updates per slot, so that each slot's
-        workspace and record arena are sized before serving (the library
-        grows buffers with synchronous allocations)."""
-        for i, slot in enumerate(self.slots):
-            r = Request(rid=-1 - i, federate=0, arrival=0.0, size=size, seed=12345 + i)
-            self._launch(slot, r)
-        for slot in self.slots:
-            slot["event"].synchronize()
-            self._finish(slot)
-        # a second round, now that each context knows its record arena size
-        for i, slot in enumerate(self.slots):
-            self._launch(slot, Request(rid=-1 - i, federate=0, arrival=0.0, size=size,
-                                       seed=54321 + i))
-        for slot in self.slots:
-            slot["event"].synchronize()
-            self._finish(slot)
+    def warm_up(self, size: Optional[int] = None, rounds: int = 2):
+        """`rounds` launches of `size` updates per slot (default: the largest
+        launch the slot limits allow), so that each slot's workspace and
+        record arena are sized before serving (the library grows buffers with
+        synchronous allocations)."""
+        if size is None:
+            per_update = self.expected_pairs(Request(0, 0, 0.0, 1, 0))
+            size = min(self.max_updates, int(0.7 * self.cap / max(per_update, 1e-9)))
+        for k in range(rounds):
+            for i, slot in enumerate(self.slots):
+                r = Request(rid=-1 - i, federate=0, arrival=0.0, size=size, seed=12345 + 97 * k + i)
+                r.est_bytes = 0
+                self._launch(slot, [r])
+            for slot in self.slots:
+                slot["event"].synchronize()
+                self._finish(slot)
+        self.launches = 0
 
     def run(self, schedule: List[Request], mover=None, step_s: float = 0.010,
             timeout_s: float = 600.0) -> List[Request]:
@@ -281,35 +369,50 @@ class Server:
             if mover_thread:
                 mover_thread.join()
 
+    def _take(self) -> List[Request]:
+        """The next launch: waiting requests in arrival order while they fit
+        the slot (updates, requests, expected pairs) and the memory budget."""
+        batch, M, pairs = [], 0, 0.0
+        while self.waiting and len(batch) < self.max_requests:
+            r = self.waiting[0]
+            if not r.est_bytes:
+                r.est_bytes = self.estimate(r)
+            if batch and (M + r.size > self.max_updates or pairs + r.est_pairs > 0.7 * self.cap):
+                break
+            if (batch or self.reserved) and self.reserved + r.est_bytes > self.budget:
+                break
+            self.waiting.pop(0)
+            self.reserved += r.est_bytes
+            r.admitted = time.perf_counter() - self.t0
+            batch.append(r)
+            M += r.size
+            pairs += r.est_pairs
+        return batch
+
     def _serve(self, schedule, timeout_s):
         pending = list(schedule)
-        waiting: List[Request] = []
+        pending.reverse()
+        self.waiting: List[Request] = []
         finished: List[Request] = []
         while len(finished) < len(schedule):
             now = time.perf_counter() - self.t0
             if now > timeout_s:
                 raise TimeoutError("serving run did not finish")
-            while pending and pending[0].arrival <= now:
-                waiting.append(pending.pop(0))
+            while pending and pending[-1].arrival <= now:
+                self.waiting.append(pending.pop())
             for slot in self.slots:  # completions
-                if slot["req"] is not None and slot["event"].query():
-                    r = slot["req"]
+                if slot["batch"] is not None and slot["event"].query():
+                    finished.extend(slot["batch"])
                     self._finish(slot)
-                    finished.append(r)
-            for slot in self.slots:  # admissions, in arrival order
-                if not waiting:
+            for slot in self.slots:  # admissions
+                if not self.waiting:
                     break
-                if slot["req"] is not None:
-                    continue
-                r = waiting[0]
-                r.est_bytes = self.estimate(r)
-                if self.reserved and self.reserved + r.est_bytes > self.budget:
-                    break
-                waiting.pop(0)
-                self.reserved += r.est_bytes
-                r.admitted = time.perf_counter() - self.t0
-                self._launch(slot, r)
-            if all(sl["req"] is not None for sl in self.slots) or not waiting:
+                if slot["batch"] is None:
+                    batch = self._take()
+                    if not batch:
+                        break
+                    self._launch(slot, batch)
+            if all(sl["batch"] is not None for sl in self.slots) or not self.waiting:
                 time.sleep(0.00005)
         return sorted(finished, key=lambda r: r.rid)
 

@@ -41,12 +41,13 @@ def test_serving_mix_equals_alone():
     import torch
     import __graft_entry__
     __graft_entry__.build()
-    d, n, l = 2, 20000, 5000.0
+    d, n, l = 2, 50000, 5000.0
     g = torch.Generator(device="cuda")
     g.manual_seed(7)
     lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
     hi = (lo + l).contiguous()
-    regions = S.ResidentRegions(lo, hi, keep_history=True)
+    # odd steps refit the idle version in place, even steps rebuild it
+    regions = S.ResidentRegions(lo, hi, keep_history=True, rebuild_every=2)
     state = {"lo": lo, "hi": hi}
     mg = torch.Generator(device="cuda")
     mg.manual_seed(11)
@@ -55,19 +56,24 @@ def test_serving_mix_equals_alone():
         state["lo"], state["hi"] = S.random_walk(state["lo"], state["hi"], 1000.0, mg)
         return state["lo"], state["hi"]
 
-    sched = S.poisson_schedule(rate=5000.0, duration=0.012, federates=8, size_lo=100,
-                               size_hi=3000, seed=3)
-    assert len(sched) >= 30
-    srv = S.Server(regions, l, slots=4, pair_capacity=1 << 20, keep_pairs=True)
+    sched = S.poisson_schedule(rate=20000.0, duration=0.01, federates=8, size_lo=1000,
+                               size_hi=200000, seed=3)
+    assert len(sched) >= 100
+    srv = S.Server(regions, l, slots=2, pair_capacity=1 << 22, keep_pairs=True)
     try:
         done = srv.run(sched, mover=mover, step_s=0.002)
     finally:
         srv.close()
-    # requests overlapped on the device
-    overlap = any(a.admitted < b.done and b.admitted < a.done
+    # launches overlapped on the device, and some launch batched several requests
+    overlap = any(a.batch != b.batch and a.admitted < b.done and b.admitted < a.done
                   for i, a in enumerate(done) for b in done[i + 1:])
     assert overlap
+    per_launch = {}
+    for r in done:
+        per_launch[r.batch] = per_launch.get(r.batch, 0) + 1
+    assert max(per_launch.values()) >= 2
     assert len({r.step for r in done}) >= 2          # the regions moved during the run
+    assert regions.refits >= 1 and regions.rebuilds >= 1
     ctx = ddm.ddm_create(0)
     try:
         for r in done:
@@ -119,4 +125,36 @@ def test_refit_state_errors():
         assert e.value.code == ddm.DDM_ERR_EXTENT
     finally:
         ddm.ddm_destroy(other)
+        ddm.ddm_destroy(ctx)
+
+
+def test_pair_offsets_of_concatenated_sets():
+    """One plan over several update sets: ddm_pair_offsets_async gives each
+    set's slice of the output laid out by update id."""
+    import torch
+    from paper_1309_3458_gb300 import workloads as W
+    a = W.uniform_fixed_length(40000, 30000, 2, 30.0, seed=5)
+    U = [torch.from_numpy(x).cuda() for x in a]
+    m = 30000
+    ctx = ddm.ddm_create(0)
+    try:
+        ddm.ddm_build(ctx, U[2], U[3])
+        offsets = torch.zeros(m + 1, dtype=torch.int64, device="cuda")
+        K = ddm.ddm_plan(ctx, U[0], U[1], offsets=offsets)
+        bounds = [0, 1, 1, 777, 12345, 29999, m, m + 5]       # the last reads as m
+        uoff = torch.tensor(bounds, dtype=torch.int64, device="cuda")
+        poff = torch.full((len(bounds),), -1, dtype=torch.int64, device="cuda")
+        ddm.ddm_pair_offsets_async(ctx, uoff, poff)
+        torch.cuda.synchronize()
+        off = offsets.cpu().numpy()
+        want = [off[min(b, m)] for b in bounds]
+        assert poff.cpu().tolist() == want
+        assert want[-1] == K
+        buf = torch.empty((K, 2), dtype=torch.int32, device="cuda")
+        ddm.ddm_write(ctx, 0, m, buf)
+        upd = buf[:, 0].cpu().numpy()
+        for i in range(len(bounds) - 2):   # slice i holds exactly updates [b_i, b_{i+1})
+            sl = upd[want[i]:want[i + 1]]
+            assert np.all((sl >= bounds[i]) & (sl < bounds[i + 1]))
+    finally:
         ddm.ddm_destroy(ctx)
