@@ -1,5 +1,6 @@
 // Host side of the C ABI (include/ddm.h): argument checks, device workspace,
 // stream-ordered launches and the single status read-back per call.
+#include <algorithm>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -46,9 +47,9 @@ struct ddm_ctx {
       blk_counter;
   uint64_t replay_budget = 0;   // bytes; 0 = never record
   uint32_t rec_blocks = 0;      // blocks of the current arena
-  // Blocks and packets of the latest recorded count pass, copied back by
-  // every plan without a host synchronisation (pinned; read as a sizing hint
-  // for the next arena, possibly one plan stale).
+  // Blocks needed, packets and blocks held by the latest recorded count
+  // pass, copied back by every plan without a host synchronisation (pinned;
+  // read as a sizing hint for the next arena, possibly one plan stale).
   volatile uint32_t* rec_hint = nullptr;
   RecordArena arena{};          // arena of the current plan (max_blocks 0 = none)
   // batched instances
@@ -324,11 +325,24 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
     const uint32_t packets = (m + 31) / 32;
     // bytes per block: records (three words each), next/count/packet/list entries
     const uint64_t per_block = (uint64_t)kRecBlock * 3 * sizeof(uint32_t) + 4 * sizeof(uint32_t);
-    const uint32_t hint_blocks = c->rec_hint[0], hint_packets = c->rec_hint[1];
-    uint64_t want = 2ull * packets;
-    if (hint_packets) {  // blocks per packet of the last pass, plus 1/8 and some slack
-      const double per_packet = (double)hint_blocks / (double)hint_packets;
-      want = (uint64_t)(per_packet * 1.125 * (double)packets) + 64;
+    // Blocks the arena holds now, and what the latest recorded pass needed.
+    uint64_t have = c->rec.cap / ((size_t)kRecBlock * 3 * sizeof(uint32_t));
+    for (const DevBuf* b : {&c->blk_next, &c->blk_count, &c->blk_pkt, &c->blk_list})
+      have = std::min<uint64_t>(have, b->cap / sizeof(uint32_t));
+    const uint32_t hint_blocks = c->rec_hint[0], hint_packets = c->rec_hint[1],
+                   hint_max = c->rec_hint[2];
+    uint64_t want = have;
+    if (have == 0 || (hint_packets && hint_blocks > hint_max)) {
+      // No arena yet, or the last pass ran out of it: size from that pass's
+      // blocks per packet (plus 1/8 and some slack), else 2 per packet.  An
+      // arena that sufficed is kept as it is: the blocks per packet depend on
+      // how densely the updates cover the space, so extrapolating them from
+      // one plan to the next would reallocate for nothing.
+      const uint64_t need =
+          hint_packets ? (uint64_t)((double)hint_blocks / (double)hint_packets * 1.125 *
+                                    (double)packets) + 64
+                       : 2ull * packets;
+      want = std::max(have, need);
     }
     const uint64_t cap_blocks = c->replay_budget / per_block;
     if (want > cap_blocks) want = cap_blocks;
@@ -341,7 +355,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
         ensure(c, c->pkt_first, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_nblk, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->pkt_off, ((size_t)packets + 1) * sizeof(unsigned long long)) == DDM_OK &&
-        ensure(c, c->blk_counter, 3 * sizeof(uint32_t)) == DDM_OK) {
+        ensure(c, c->blk_counter, 4 * sizeof(uint32_t)) == DDM_OK) {
       c->arena.rec = static_cast<uint32_t*>(c->rec.p);
       c->arena.blk_next = static_cast<uint32_t*>(c->blk_next.p);
       c->arena.blk_count = static_cast<uint32_t*>(c->blk_count.p);
@@ -352,7 +366,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
       c->arena.pkt_off = static_cast<unsigned long long*>(c->pkt_off.p);
       c->arena.blk_counter = static_cast<uint32_t*>(c->blk_counter.p);
       c->arena.max_blocks = (uint32_t)want;
-      DDM_CUDA(cudaMemsetAsync(c->blk_counter.p, 0, 3 * sizeof(uint32_t), s));
+      DDM_CUDA(cudaMemsetAsync(c->blk_counter.p, 0, 4 * sizeof(uint32_t), s));
     }
   }
   if (m > 0) {
@@ -380,9 +394,9 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
     DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets, c->arena.pkt_off, sums, nullptr, s));
     DDM_CUDA(launch_block_list(c->arena, packets, s));
   }
-  if (c->arena.max_blocks)  // blocks needed and packets, the next arena's sizing hint
+  if (c->arena.max_blocks)  // blocks needed, packets, blocks held: the next arena's sizing hint
     DDM_CUDA(cudaMemcpyAsync((void*)c->rec_hint, static_cast<uint32_t*>(c->blk_counter.p) + 1,
-                             2 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+                             3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
   c->ulo = ulo;
   c->uhi = uhi;
   c->flags = flags;
@@ -494,12 +508,12 @@ int ddm_create(ddm_ctx** out, int device) {
   if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&c->st_dev, sizeof(Status)) != cudaSuccess ||
       cudaMallocHost(&c->st_host, sizeof(Status)) != cudaSuccess ||
-      cudaMallocHost((void**)&c->rec_hint, 2 * sizeof(uint32_t)) != cudaSuccess) {
+      cudaMallocHost((void**)&c->rec_hint, 3 * sizeof(uint32_t)) != cudaSuccess) {
     cudaGetLastError();
     ddm_destroy(c);
     return DDM_ERR_NOMEM;
   }
-  c->rec_hint[0] = c->rec_hint[1] = 0;
+  c->rec_hint[0] = c->rec_hint[1] = c->rec_hint[2] = 0;
   *out = c;
   return DDM_OK;
 }

@@ -189,7 +189,8 @@ struct RecordArena {
   unsigned long long* pkt_off;  // [packets + 1] exclusive prefix of pkt_nblk
   uint32_t* blk_list;      // [max_blocks] blocks in plan order
   uint32_t* blk_counter;   // [0] blocks handed out (may exceed max_blocks),
-                           // [1] blocks the whole pass needed, [2] packets
+                           // [1] blocks the whole pass needed, [2] packets,
+                           // [3] max_blocks (the last two for arena sizing)
   uint32_t max_blocks;     // 0: no recording
 };
 // The records of the last count pass are complete (the write pass may

@@ -397,7 +397,10 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
 
 // Plan-order list of record blocks: one thread per packet copies its chain.
 __global__ void k_block_list(RecordArena ra, uint32_t packets) {
-  if (blockIdx.x == 0 && threadIdx.x == 0) ra.blk_counter[2] = packets;  // sizing hint
+  if (blockIdx.x == 0 && threadIdx.x == 0) {  // sizing hint for the next arena
+    ra.blk_counter[2] = packets;
+    ra.blk_counter[3] = ra.max_blocks;
+  }
   if (!records_complete(ra)) return;
   for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < packets;
        p += gridDim.x * blockDim.x) {
