@@ -40,7 +40,7 @@ DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
 # DRAM bytes (read + write) per pair of the write-pass kernel (k_replay), from
 # the ncu capture summarised in profiles/k_replay_clustered_d3_scale0.15.md
 # (a smaller case of the same workload; traffic scales with pairs written).
-TRAFFIC_PER_PAIR = 9.96
+TRAFFIC_PER_PAIR = 9.65
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -586,12 +586,12 @@ def main():
         "queries_per_s": m * args.steps * world / t_job,
         "p50_ms": float(np.percentile(step_ms, 50)),
         "p99_ms": float(np.percentile(step_ms, 99)),
-        "roofline": {"bound": "hbm", "kernel": "k_packets<write> (ddm_write_ordered)",
+        "roofline": {"bound": "hbm", "kernel": "k_replay (ddm_write_ordered)",
                      "achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": write_gbs / hbm_peak,
                      "traffic": TRAFFIC_PER_PAIR * sum(write_pairs) / max(1, len(write_pairs)),
-                     "traffic_note": "bytes per launch, scaled from an ncu capture of a smaller "
-                                     "case by pairs written (see DESIGN.md, profiles/)",
+                     "traffic_note": "bytes per launch, scaled by pairs written from an ncu "
+                                     "capture of the same workload at scale 0.15",
                      "peak_source": peak_src,
                      "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 8*(pairs in chunk)",
                      "write_ms_per_step": 1e3 * write_s / args.steps},

@@ -409,37 +409,57 @@ __global__ void k_block_list(RecordArena ra, uint32_t packets) {
   }
 }
 
+// L2 eviction-priority hints (PTX createpolicy / .L2::cache_hint): the pairs
+// and the records stream through L2 once and are marked evict-first, so that
+// they do not push the subscription ids (reused by every record that names
+// their leaf) out of L2; the id loads are marked evict-last.
+__device__ __forceinline__ unsigned long long l2_policy_evict_last() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ unsigned long long l2_policy_evict_first() {
+  unsigned long long p;
+  asm("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+__device__ __forceinline__ uint32_t ld_hinted(const uint32_t* a, unsigned long long policy) {
+  uint32_t v;
+  asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(policy));
+  return v;
+}
+__device__ __forceinline__ void st_hinted(ddm_pair* a, ddm_pair v, unsigned long long policy) {
+  asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(a), "r"(v.upd),
+               "r"(v.sub), "l"(policy)
+               : "memory");
+}
+
 // Write pass from the records of the count pass.  Work unit: one record
 // block (up to 512 records of one packet), taken from the plan-order block
 // list, so uneven packets spread over the whole GPU.  A warp loads the
 // block's packet queries (their output offsets) and takes the records 32 at
-// a time, one per lane.  Each lane works out where its record's pairs go
-// (its query's offset plus the matches the count pass had found before the
-// record); an exclusive scan over the lanes gives every pair of the 32
-// records a slot in a per-warp staging buffer in shared memory, into which
-// each lane writes its own record's pairs (one per set bit of the hit mask)
-// together with their output positions.  The warp then copies the buffer
-// out, lane = pair: each store instruction writes 32 consecutive staged
-// pairs, which form a few contiguous runs of the output -- the positions the
-// walking write pass would use.  Positions are relative to the range's first
-// pair; with fewer than 2^32 pairs in the range (WIDE false) they are 32-bit.
-// Staged pairs per warp: 32 records hold at most 1,024 pairs, so two rounds
-// at most (four with 64-bit positions).
-template <bool WIDE>
-struct ReplayBuf {
-  static constexpr int kPairs = WIDE ? 256 : 512;
-};
-
+// a time (the next 32 are loaded while these expand), one per lane: each lane
+// works out where its record's pairs go (its query's offset plus the matches
+// the count pass had found before the record) and leaves (leaf, hit mask,
+// update id, position) in shared memory.  The warp then expands the 32
+// records one after another with lane = leaf slot, each record's fields read
+// by one broadcast from shared memory: the lanes whose bit is set in the hit
+// mask load their subscription ids (one 128-byte load for the whole leaf) and
+// store their pairs at the record's position plus their rank among the set
+// bits -- one contiguous run of the output per record.  Eight records are in
+// flight at a time (their id loads issued before their stores).  Positions
+// are relative to the range's first pair; with fewer than 2^32 pairs in the
+// range (WIDE false) they are 32-bit.
 template <bool FILTER_ID, bool WIDE, bool BATCH>
 __global__ void __launch_bounds__(kThreads, 4)
 k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uint32_t p0,
          uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
          uint32_t* __restrict__ work, Status* __restrict__ st) {
   using Cursor = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-  constexpr int kReplayBuf = ReplayBuf<WIDE>::kPairs;
-  __shared__ ddm_pair s_pair[kWarps][kReplayBuf];
-  __shared__ Cursor s_pos[kWarps][kReplayBuf];
+  __shared__ uint4 s_rec[kWarps][32];   // leaf, hit mask, update id, subscription id base
+  __shared__ Cursor s_at[kWarps][32];   // output position of the record's first pair
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const uint32_t below = (1u << lane) - 1u;  // lanes below this one
   if (!records_complete(ra)) return;  // the walking write pass handles this range
   const unsigned long long base0 = w.start[w.b_idx];
   const unsigned long long need = w.start[w.e_idx] - base0;
@@ -453,6 +473,9 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
   // stay below need <= capacity.
   if (need > w.capacity) return;
   if (!WIDE && need > 0xffffffffull) return;  // host picks WIDE for such ranges
+  ddm_pair* __restrict__ pairs = w.pairs;
+  const uint32_t* __restrict__ sid = t.sid;
+  const unsigned long long keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
   const unsigned long long i0 = ra.pkt_off[p0], i1 = ra.pkt_off[p1];
   for (;;) {
     unsigned long long i = 0;
@@ -478,47 +501,50 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     if (vmask == 0u) continue;
     const uint32_t nrec = ra.blk_count[blk];
     const uint32_t* rec = ra.rec + (size_t)blk * (3u * kRecBlock);
+    uint32_t nx = 0u, nhb = 0u, nbef = 0u;
+    if (lane < nrec) {
+      nx = ld_hinted(&rec[lane], stream);
+      nhb = ld_hinted(&rec[kRecBlock + lane], stream);
+      nbef = ld_hinted(&rec[2u * kRecBlock + lane], stream);
+    }
     for (uint32_t r0 = 0; r0 < nrec; r0 += 32u) {
-      const bool rv = r0 + lane < nrec;
-      const uint32_t x = rv ? rec[r0 + lane] : 0u;
-      uint32_t hb = rv ? rec[kRecBlock + r0 + lane] : 0u;
-      const uint32_t bef = rv ? rec[2u * kRecBlock + r0 + lane] : 0u;
+      const uint32_t x = nx, bef = nbef;
+      uint32_t hb = nhb;
+      if (r0 + 32u + lane < nrec) {
+        nx = ld_hinted(&rec[r0 + 32u + lane], stream);
+        nhb = ld_hinted(&rec[kRecBlock + r0 + 32u + lane], stream);
+        nbef = ld_hinted(&rec[2u * kRecBlock + r0 + 32u + lane], stream);
+      }
       const int qq = (int)(x & 31u);
-      if (!((vmask >> qq) & 1u)) hb = 0u;
-      const uint32_t c = __popc(hb);
+      if (!((vmask >> qq) & 1u)) hb = 0u;  // also clears lanes past nrec (x = hb = 0)
       const Cursor o = __shfl_sync(0xffffffffu, out, qq) + (Cursor)bef;
       const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
       const uint32_t sb = BATCH ? __shfl_sync(0xffffffffu, sub_base, qq) : 0u;
-      uint32_t incl = c;  // inclusive scan of the pair counts over the lanes
+      __syncwarp();  // the previous round has read s_rec / s_at
+      s_rec[wib][lane] = make_uint4(x >> 5, hb, Qq, sb);
+      s_at[wib][lane] = o;
+      __syncwarp();
+#pragma unroll 1
+      for (int g = 0; g < 32; g += 8) {
+        uint32_t hr[8], sv[8];
 #pragma unroll
-      for (int d2 = 1; d2 < 32; d2 <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, d2);
-        if (lane >= d2) incl += y;
-      }
-      const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
-      const uint32_t excl = incl - c;
-      const uint32_t* sid_leaf = t.sid + (x >> 5) * 32u;
-      for (uint32_t base = 0; base < total; base += kReplayBuf) {
-        // stage: every lane writes its record's pairs that fall in this round
-        uint32_t m = hb, k = 0;
-        while (m) {
-          const uint32_t bit = __ffs(m) - 1u;
-          m &= m - 1u;
-          const uint32_t slot = excl + k - base;  // wraps for slots before base
-          if (slot < (uint32_t)kReplayBuf) {
-            ddm_pair pr;
-            pr.upd = Qq;
-            pr.sub = sid_leaf[bit] - sb;
-            s_pair[wib][slot] = pr;
-            s_pos[wib][slot] = o + (Cursor)k;
-          }
-          ++k;
+        for (int u = 0; u < 8; ++u) {
+          const uint2 a = *reinterpret_cast<const uint2*>(&s_rec[wib][g + u]);
+          hr[u] = a.y;
+          sv[u] = 0u;
+          if ((hr[u] >> lane) & 1u) sv[u] = ld_hinted(sid + a.x * 32u + (uint32_t)lane, keep);
         }
-        __syncwarp();
-        const uint32_t nround = min((uint32_t)kReplayBuf, total - base);
-        for (uint32_t tt = lane; tt < nround; tt += 32u)
-          w.pairs[(unsigned long long)s_pos[wib][tt]] = s_pair[wib][tt];
-        __syncwarp();
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const uint4 a = s_rec[wib][g + u];
+          const Cursor at = s_at[wib][g + u];
+          if ((hr[u] >> lane) & 1u) {
+            ddm_pair pr;
+            pr.upd = a.z;
+            pr.sub = sv[u] - a.w;
+            st_hinted(pairs + (unsigned long long)(at + (Cursor)__popc(hr[u] & below)), pr, stream);
+          }
+        }
       }
     }
   }
