@@ -67,6 +67,7 @@ def parse():
     ap.add_argument("--no-serving", action="store_true", help="skip the serving run")
     ap.add_argument("--serving-only", action="store_true", help="run only the serving run")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
+    ap.add_argument("--no-sweep", action="store_true", help="skip the alpha x N sweep")
     return ap.parse_args()
 
 
@@ -387,6 +388,41 @@ def serving_section(seconds: float = 2.0, slots: int = 4, saturated_seconds: flo
     return out
 
 
+def sweep_section(reps: int = 3):
+    """The shape of the paper's Fig. 7 (Section V): d = 1 uniform workloads,
+    N = n + m in {5e4, 1e5, 2.5e5, 5e5}, overlapping degree alpha in
+    {1, 10, 50, 100}; one full match (build, count, write) per point, median
+    of `reps` timed with CUDA events after one warm-up."""
+    import torch
+
+    import paper_1309_3458_gb300 as ddm
+    from paper_1309_3458_gb300 import workloads as W
+    ctx = ddm.ddm_create(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = []
+    try:
+        for N in (50_000, 100_000, 250_000, 500_000):
+            for alpha in (1.0, 10.0, 50.0, 100.0):
+                a = W.uniform_fixed_length(N - N // 2, N // 2, 1, alpha, seed=7)
+                U = [torch.from_numpy(x).cuda() for x in a]
+                K = ddm.ddm_count(ctx, *U)
+                buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+                ddm.ddm_match(ctx, *U, buf)
+                ts = []
+                for _ in range(reps):
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    ddm.ddm_match(ctx, *U, buf)
+                    e1.record(stream)
+                    e1.synchronize()
+                    ts.append(e0.elapsed_time(e1))
+                ts.sort()
+                out.append({"N": N, "alpha": alpha, "K": K, "ms": round(ts[len(ts) // 2], 4)})
+    finally:
+        ddm.ddm_destroy(ctx)
+    return out
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -503,28 +539,44 @@ def main():
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     # ---- end to end with host buffers ----
+    # Inputs are copied from pinned host memory every step and every pair is
+    # copied back to pinned host memory.  The device pair buffer is split in
+    # two halves: while one half's pairs travel to the host on a copy stream,
+    # the next chunk is written into the other half.
     e2e = None
     if not args.no_e2e:
         host = [torch.from_numpy(a).pin_memory() for a in arrays]
         stage = torch.empty((int(args.stage_gb * 1e9) // 8, 2), dtype=torch.int32).pin_memory()
         h2d = sum(a.nbytes for a in arrays)
         e2e_steps = args.e2e_steps or max(1, min(args.steps, 3))
+        half = cap // 2
+        bufs = (pairs[:half], pairs[half:2 * half])
+        copy_stream = torch.cuda.Stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
 
         def e2e_step():
             for t_dev, t_host in zip(dev, host):
                 t_dev.copy_(t_host, non_blocking=True)
             ddm.ddm_build(ctx, dev[2], dev[3])
             Ke = ddm.ddm_plan(ctx, dev[0], dev[1])
-            b = 0
+            b, i = 0, 0
             while b < m:
-                e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
-                k = ddm.ddm_write_ordered(ctx, b, e, pairs)
-                o = 0
-                while o < k:
-                    c = min(stage.shape[0], k - o)
-                    stage[:c].copy_(pairs[o:o + c], non_blocking=True)
-                    o += c
-                b = e
+                e = ddm.ddm_chunk_end_ordered(ctx, b, half)
+                buf = bufs[i % 2]
+                stream.wait_event(copied[i % 2])      # that half's previous pairs are out
+                k = ddm.ddm_write_ordered(ctx, b, e, buf)
+                written = torch.cuda.Event()
+                written.record(stream)
+                copy_stream.wait_event(written)
+                with torch.cuda.stream(copy_stream):
+                    o = 0
+                    while o < k:
+                        c = min(stage.shape[0], k - o)
+                        stage[:c].copy_(buf[o:o + c], non_blocking=True)
+                        o += c
+                    copied[i % 2].record(copy_stream)
+                b, i = e, i + 1
+            stream.wait_stream(copy_stream)
             torch.cuda.synchronize()
             return Ke
 
@@ -558,6 +610,10 @@ def main():
     if not args.no_serving and world == 1:
         torch.cuda.empty_cache()
         serving = serving_section(args.serving_seconds)
+
+    sweep = None
+    if not args.no_sweep and world == 1:
+        sweep = sweep_section()
 
     cpu = None
     if not args.no_cpu and world == 1:
@@ -605,6 +661,7 @@ def main():
         "clocks": clocks,
         "batched": batched,
         "serving": serving,
+        "alpha_n_sweep": sweep,
     }
     print(json.dumps(line), flush=True)
 

@@ -34,8 +34,9 @@
  *    synchronise `stream` once to read it; nothing else blocks the host.
  *  - Output pairs are written to caller-owned DEVICE memory.  Order: update
  *    id ascending, then the subscriptions' position in the tree (for d = 1
- *    that is dimension-0 lower, upper, id).  Only the set of pairs is the
- *    result; the order is deterministic for a given input.
+ *    that is dimension-0 lower, upper, id); with DDM_SWAP_ROLES subscription
+ *    id ascending, then the updates' tree position.  Only the set of pairs
+ *    is the result; the order is deterministic for a given input.
  *  - Sizes: 1 <= d <= DDM_MAX_DIMS, n and m <= DDM_MAX_EXTENTS; n == 0 or
  *    m == 0 is valid and gives K = 0.
  *  - A context is not thread safe: one host thread at a time per context.
@@ -62,6 +63,13 @@ extern "C" {
 /* Flags. */
 #define DDM_CLOSED 0u  /* default: closed segments, x.lo <= y.hi && y.lo <= x.hi */
 #define DDM_OPEN   1u  /* Alg. 1 as printed: x.lo < y.hi && y.lo < x.hi */
+/* One-shot calls only (ddm_count, ddm_match, ddm_match_range over the whole
+ * update range): build the tree over the UPDATE set and run one query per
+ * subscription -- the roles of the two sets swapped, as Section IV allows
+ * for building over the smaller set.  The pair set is the same (pairs still
+ * read {upd, sub}); they come grouped by subscription id instead of by
+ * update id. */
+#define DDM_SWAP_ROLES 2u
 
 #define DDM_MAX_DIMS    8
 #define DDM_MAX_EXTENTS 1073741823u  /* 2^30 - 1 per set */
@@ -119,7 +127,7 @@ int ddm_match(ddm_ctx *ctx, int d,
  * global).  For outputs larger than device memory, call repeatedly over
  * consecutive ranges, or use the staged calls below, which avoid redoing
  * the tree.  Errors as ddm_match, plus DDM_ERR_ARG when the range is not
- * within [0, m]. */
+ * within [0, m], or with DDM_SWAP_ROLES unless the range is [0, m). */
 int ddm_match_range(ddm_ctx *ctx, int d,
                     const float *upd_lo, const float *upd_hi, uint32_t m,
                     const float *sub_lo, const float *sub_hi, uint32_t n,

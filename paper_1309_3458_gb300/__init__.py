@@ -32,6 +32,7 @@ DDM_ERR_STATE = 7
 
 DDM_CLOSED = 0
 DDM_OPEN = 1
+DDM_SWAP_ROLES = 2
 DDM_MAX_DIMS = 8
 DDM_MAX_EXTENTS = (1 << 30) - 1
 DDM_MAX_TREE_LEVELS = 8

@@ -1,6 +1,7 @@
 // Host side of the C ABI (include/ddm.h): argument checks, device workspace,
 // stream-ordered launches and the single status read-back per call.
 #include <algorithm>
+#include <utility>
 #include <atomic>
 #include <cstdlib>
 #include <cstring>
@@ -62,6 +63,7 @@ struct ddm_ctx {
 
   bool built = false;
   bool attached = false;        // tree borrowed from another context (ddm_attach)
+  bool swapped = false;         // one-shot call with DDM_SWAP_ROLES: tree over the updates
   TreeView tree{};
   bool planned = false;
   const float* ulo = nullptr;
@@ -255,6 +257,7 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
                 const BatchSet* bs = nullptr) {
   c->built = false;
   c->attached = false;
+  c->swapped = false;
   if (!bs) c->bv = BatchView{};
   c->planned = false;
   TreeView t{};
@@ -422,6 +425,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
     WriteView w{};
     w.start = static_cast<const unsigned long long*>(c->offsets.p);
     w.by_pos = false;
+    w.swap = c->swapped;
     w.b_idx = begin;
     w.e_idx = end;
     w.pairs = pairs;
@@ -717,22 +721,31 @@ static int match_impl(ddm_ctx* c, int d, const float* ulo, const float* uhi, uin
                       uint32_t flags, ddm_pair* pairs, uint64_t capacity, uint64_t* k_out,
                       void* stream, bool write) {
   if (!c || d < 1 || d > DDM_MAX_DIMS || !set_ok(d, ulo, uhi, m) || !set_ok(d, slo, shi, n) ||
-      (flags & ~DDM_OPEN) || begin > end || end > m)
+      (flags & ~(DDM_OPEN | DDM_SWAP_ROLES)) || begin > end || end > m)
     return DDM_ERR_ARG;
+  const bool swap = (flags & DDM_SWAP_ROLES) != 0;
+  if (swap && (begin != 0 || end != m)) return DDM_ERR_ARG;
+  if (write && end > begin && !pairs && capacity > 0) return DDM_ERR_ARG;
+  if (swap) {  // tree over the updates, one query per subscription
+    std::swap(ulo, slo);
+    std::swap(uhi, shi);
+    std::swap(m, n);
+    begin = 0;
+    end = m;
+  }
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(build_async(c, d, slo, shi, n, s));
-  DDM_TRY(plan_async(c, ulo, uhi, m, flags, write, s));
-  if (write) {
-    if (end > begin && !pairs && capacity > 0) return DDM_ERR_ARG;
-    DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
-  }
+  c->swapped = swap;
+  DDM_TRY(plan_async(c, ulo, uhi, m, flags & DDM_OPEN, write, s));
+  if (write) DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
   DDM_TRY(sync_status(c, s));
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
-  if (rc == DDM_ERR_EXTENT || rc == DDM_ERR_TIMEOUT) c->built = c->planned = false;
+  // a swapped problem's tree and plan are not the caller's sets: no staged use
+  if (swap || rc == DDM_ERR_EXTENT || rc == DDM_ERR_TIMEOUT) c->built = c->planned = false;
   return rc;
 }
 

@@ -62,6 +62,7 @@ struct QueryView {
 struct WriteView {
   const unsigned long long* start;
   bool by_pos;
+  bool swap;  // roles swapped: the tree holds the updates, queries are subscriptions
   uint32_t b_idx, e_idx;
   ddm_pair* pairs;
   unsigned long long capacity;

@@ -268,6 +268,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
                 ddm_pair pr;
                 pr.upd = Qq;
                 pr.sub = my_sid - sub_base;
+                if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
                 w.pairs[at] = pr;
               }
             }
@@ -542,6 +543,7 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
             ddm_pair pr;
             pr.upd = a.z;
             pr.sub = sv[u] - a.w;
+            if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
             st_hinted(pairs + (unsigned long long)(at + (Cursor)__popc(hr[u] & below)), pr, stream);
           }
         }

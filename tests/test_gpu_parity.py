@@ -351,3 +351,55 @@ def test_capacity_and_state_errors(ctx):
     with pytest.raises(ddm.DDMError) as e:
         ddm.ddm_count(ctx, *bad)
     assert e.value.code == ddm.DDM_ERR_ARG
+
+
+@pytest.mark.parametrize("d", [1, 2, 3])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_swap_roles_same_pairs(ctx, d, flags):
+    """DDM_SWAP_ROLES (tree over the updates, one query per subscription;
+    Section IV lets the tree be built over either set) reports the same pair
+    set, grouped by subscription id."""
+    import torch
+    for n, m, seed in ((2500, 400, 3), (300, 3100, 4)):
+        arrays = W.uniform_fixed_length(n, m, d, 40.0, seed=seed)
+        if seed == 4:   # ties and infinities in the mix
+            g = W.grid_random(n, m, d, seed=seed, grid=7)
+            arrays = g
+            arrays[3][0, :5] = np.inf
+            arrays[0][0, :5] = -np.inf
+        U = to_dev(arrays)
+        K = ddm.ddm_count(ctx, *U, flags=flags)
+        Ks = ddm.ddm_count(ctx, *U, flags=flags | ddm.DDM_SWAP_ROLES)
+        assert Ks == K
+        pairs = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+        assert ddm.ddm_match(ctx, *U, pairs, flags=flags | ddm.DDM_SWAP_ROLES) == K
+        got = pairs[:K].cpu().numpy().view(np.uint32)
+        assert (np.diff(got[:, 1].astype(np.int64)) >= 0).all()   # grouped by subscription
+        Ko, ou, os_ = oracle.itm_pairs(*arrays, flags=flags)
+        assert Ko == K
+        assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(ou, os_)))
+
+
+def test_swap_roles_limits(ctx):
+    import torch
+    arrays = W.uniform_fixed_length(500, 300, 2, 10.0, seed=9)
+    U = to_dev(arrays)
+    pairs = torch.empty((1 << 16, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(ddm.DDMError) as e:   # a partial update range has no meaning swapped
+        ddm.ddm_match_range(ctx, *U, 10, 20, pairs, flags=ddm.DDM_SWAP_ROLES)
+    assert e.value.code == ddm.DDM_ERR_ARG
+    K = ddm.ddm_match_range(ctx, *U, 0, 300, pairs, flags=ddm.DDM_SWAP_ROLES)
+    replayed = pairs[:K].cpu().numpy().copy()
+    other = ddm.ddm_create(0)
+    try:   # the walking write pass (no record arena) swaps the same way
+        ddm.ddm_set_replay_budget(other, 0)
+        assert ddm.ddm_match(other, *U, pairs, flags=ddm.DDM_SWAP_ROLES) == K
+        assert np.array_equal(pairs[:K].cpu().numpy(), replayed)
+    finally:
+        ddm.ddm_destroy(other)
+    with pytest.raises(ddm.DDMError) as e:   # the swapped tree is not left for staged calls
+        ddm.ddm_plan(ctx, U[0], U[1])
+    assert e.value.code == ddm.DDM_ERR_STATE
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.ddm_plan(ctx, U[0], U[1], flags=ddm.DDM_SWAP_ROLES)
+    assert e.value.code in (ddm.DDM_ERR_ARG, ddm.DDM_ERR_STATE)
