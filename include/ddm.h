@@ -210,6 +210,26 @@ int ddm_plan_async(ddm_ctx *ctx, const float *upd_lo, const float *upd_hi, uint3
 int ddm_write_async(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end, ddm_pair *pairs,
                     uint64_t capacity, uint64_t *k_dev, uint32_t *err_dev, void *stream);
 
+/* Dynamic interval management (Section IV): with a tree over one set kept
+ * current (ddm_build, then ddm_refit as its extents move), the row (or
+ * column) of every extent of the other set that moved is recomputed by one
+ * query against that tree.  This call matches k moved extents (lo, hi:
+ * DEVICE SoA of d x k floats, their new coordinates) against the context's
+ * tree and writes all their pairs, each moved extent named by ids[j]
+ * (DEVICE, k entries; NULL: j itself):
+ *  - flags without DDM_SWAP_ROLES: the tree holds the subscriptions and the
+ *    moved extents are updates; pairs read {ids[j], subscription id};
+ *  - with DDM_SWAP_ROLES: the tree holds the updates and the moved extents
+ *    are subscriptions; pairs read {update id, ids[j]};
+ *  DDM_OPEN selects the open rule.  Pairs are grouped by moved extent (in
+ * the order 0..k-1).  *k_out = pair count; DDM_ERR_CAPACITY as ddm_match.
+ * Replaces the context's plan; the tree is unchanged.  Synchronises
+ * `stream` once.  Errors: DDM_ERR_ARG, DDM_ERR_STATE (no tree),
+ * DDM_ERR_EXTENT, DDM_ERR_CAPACITY, DDM_ERR_NOMEM, DDM_ERR_CUDA. */
+int ddm_match_moved(ddm_ctx *ctx, const float *lo, const float *hi, uint32_t k,
+                    const uint32_t *ids, uint32_t flags, ddm_pair *pairs, uint64_t capacity,
+                    uint64_t *k_out, void *stream);
+
 /* Output offsets of update-id boundaries, for one plan that matches several
  * update sets at once (concatenated, set r holding update ids
  * [upd_off[r], upd_off[r+1])): pair_off[i] = number of pairs of the updates

@@ -56,6 +56,7 @@ SIGNATURES = {
     "ddm_plan_async": (_i, [_vp, _vp, _vp, _u32, _u32, _vp]),
     "ddm_write_async": (_i, [_vp, _u32, _u32, _vp, _u64, _vp, _vp, _vp]),
     "ddm_pair_offsets_async": (_i, [_vp, _vp, _u32, _vp, _vp]),
+    "ddm_match_moved": (_i, [_vp, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp, _vp]),
     "ddm_attach": (_i, [_vp, _vp]),
     "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
@@ -215,6 +216,21 @@ def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, e
     cap = 0 if pairs is None else pairs.shape[0]
     _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, _ptr(k_dev),
                                  _ptr(err_dev), _stream(stream)), "ddm_write_async")
+
+
+def ddm_match_moved(ctx: int, lo, hi, ids, pairs, flags: int = DDM_CLOSED, stream=None) -> int:
+    """Pairs of k moved extents (d x k device tensors) against the context's
+    tree, the moved extents named by ids (uint32/int32 device tensor of k
+    entries, or None for 0..k-1); see ddm.h."""
+    d, l, h, k = _set(lo, hi)
+    if ids is not None and ids.shape[0] != k:
+        raise ValueError("ids needs one entry per moved extent")
+    cap = 0 if pairs is None else pairs.shape[0]
+    kk = ctypes.c_uint64(0)
+    rc = lib().ddm_match_moved(ctx, l, h, k, _ptr(ids), flags, _ptr(pairs), cap,
+                               ctypes.byref(kk), _stream(stream))
+    _check(rc, "ddm_match_moved", kk.value)
+    return kk.value
 
 
 def ddm_pair_offsets_async(ctx: int, upd_off, pair_off, stream=None) -> None:

@@ -409,7 +409,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
 
 // Write pass for updates with ids in [begin, end), laid out by update id.
 int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
-                cudaStream_t s) {
+                cudaStream_t s, const uint32_t* qids = nullptr) {
   if (end > begin && c->tree.n > 0) {
     QueryView q = query_view(c);
     if (begin != 0 || end != c->m) {
@@ -426,6 +426,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
     w.start = static_cast<const unsigned long long*>(c->offsets.p);
     w.by_pos = false;
     w.swap = c->swapped;
+    w.qids = qids;
     w.b_idx = begin;
     w.e_idx = end;
     w.pairs = pairs;
@@ -655,6 +656,31 @@ int ddm_write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, u
   if (err_dev)
     DDM_CUDA(cudaMemcpyAsync(err_dev, &c->st_dev->err, sizeof(uint32_t), cudaMemcpyDeviceToDevice, s));
   return DDM_OK;
+}
+
+int ddm_match_moved(ddm_ctx* c, const float* lo, const float* hi, uint32_t k, const uint32_t* ids,
+                    uint32_t flags, ddm_pair* pairs, uint64_t capacity, uint64_t* k_out,
+                    void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->built || c->bv.count) return DDM_ERR_STATE;
+  if (!set_ok(c->tree.d, lo, hi, k) || (flags & ~(DDM_OPEN | DDM_SWAP_ROLES)) ||
+      (k > 0 && !pairs && capacity > 0))
+    return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(plan_async(c, lo, hi, k, flags & DDM_OPEN, true, s));
+  const bool was = c->swapped;
+  c->swapped = (flags & DDM_SWAP_ROLES) != 0;
+  const int wrc = write_async(c, 0, k, pairs, capacity, s, ids);
+  c->swapped = was;
+  DDM_TRY(wrc);
+  DDM_TRY(sync_status(c, s));
+  if (k_out) *k_out = c->st_host->K;
+  const int rc = status_code(*c->st_host);
+  if (rc != DDM_OK) c->planned = false;
+  return rc;
 }
 
 int ddm_pair_offsets_async(ddm_ctx* c, const uint64_t* upd_off, uint32_t count, uint64_t* pair_off,

@@ -63,6 +63,7 @@ struct WriteView {
   const unsigned long long* start;
   bool by_pos;
   bool swap;  // roles swapped: the tree holds the updates, queries are subscriptions
+  const uint32_t* qids;  // optional: id written for query q is qids[q] (else q)
   uint32_t b_idx, e_idx;
   ddm_pair* pairs;
   unsigned long long capacity;
