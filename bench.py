@@ -388,6 +388,27 @@ def serving_section(seconds: float = 2.0, slots: int = 4, saturated_seconds: flo
     return out
 
 
+# ALU pipe of one GB300: 152 SMs x 64 lanes (16 per sub-partition; ncu's
+# own ALU-pipe peak, 0.5 warp instructions per cycle per sub-partition) at
+# the 2,070 MHz maximum SM clock; a float compare is one lane operation.
+ALU_PEAK_GCMP = 152 * 64 * 2.070
+
+
+def count_roofline(leaf_tests, d, count_ms, steps):
+    """The count pass (`k_packets`, issue / ALU bound): segment comparisons
+    the tree walk makes -- 2d per tested subscription, 32 subscriptions per
+    (query, leaf) test, counted by the kernel itself -- per second of
+    ddm_plan (update sort + count pass + scans; the count pass is about 97%
+    of it), against the ALU pipe's compare rate."""
+    sec = sum(a.elapsed_time(b) for a, b in count_ms) / 1e3 / max(1, steps)
+    cmp = float(leaf_tests) * 32 * 2 * d
+    achieved = cmp / sec / 1e9 if sec > 0 else 0.0
+    return {"bound": "alu", "kernel": "k_packets (count pass, ddm_plan)", "achieved": achieved,
+            "peak": ALU_PEAK_GCMP, "unit": "Gcmp/s", "frac": achieved / ALU_PEAK_GCMP,
+            "leaf_tests": int(leaf_tests), "plan_ms_per_step": 1e3 * sec,
+            "peak_source": "unit counts x max SM clock"}
+
+
 def sweep_section(reps: int = 3):
     """The shape of the paper's Fig. 7 (Section V): d = 1 uniform workloads,
     N = n + m in {5e4, 1e5, 2.5e5, 5e5}, overlapping degree alpha in
@@ -478,18 +499,24 @@ def main():
     pairs = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
     stream = torch.cuda.current_stream()
 
-    write_ms, write_bytes, write_pairs, plan_ms = [], [], [], []
+    write_ms, write_bytes, write_pairs, plan_ms, count_ms = [], [], [], [], []
     chunks = [0]
+    tests = [0]
 
     def step(record=False):
         if record:
             a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a0.record(stream)
         ddm.ddm_build(ctx, dev[2], dev[3])
+        if record:
+            ab = torch.cuda.Event(enable_timing=True)
+            ab.record(stream)
         K = ddm.ddm_plan(ctx, dev[0], dev[1])
         if record:
             a1.record(stream)
             plan_ms.append((a0, a1))
+            count_ms.append((ab, a1))
+            tests[0] = ddm.ddm_plan_stats(ctx)
         b = 0
         chunks[0] = 0
         while b < m:
@@ -651,6 +678,7 @@ def main():
                      "peak_source": peak_src,
                      "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 8*(pairs in chunk)",
                      "write_ms_per_step": 1e3 * write_s / args.steps},
+        "roofline_count": count_roofline(tests[0], d, count_ms, args.steps),
         "phases_ms_per_step": {
             "build_and_count": sum(a.elapsed_time(b) for a, b in plan_ms) / args.steps,
             "write": 1e3 * write_s / args.steps,

@@ -210,6 +210,14 @@ int ddm_plan_async(ddm_ctx *ctx, const float *upd_lo, const float *upd_hi, uint3
 int ddm_write_async(ddm_ctx *ctx, uint32_t upd_begin, uint32_t upd_end, ddm_pair *pairs,
                     uint64_t capacity, uint64_t *k_dev, uint32_t *err_dev, void *stream);
 
+/* Work of the last count pass that returned to the host (ddm_count,
+ * ddm_match, ddm_match_range, ddm_plan, ddm_batch_match, ddm_match_moved):
+ * *leaf_tests = the (query, leaf) tests it made, each one query against the
+ * 32 subscriptions of a leaf whose box meets the query's (2d segment
+ * comparisons per subscription, Section III-A).  For measurement; the paper
+ * has no counterpart. */
+int ddm_plan_stats(ddm_ctx *ctx, uint64_t *leaf_tests);
+
 /* Dynamic interval management (Section IV): with a tree over one set kept
  * current (ddm_build, then ddm_refit as its extents move), the row (or
  * column) of every extent of the other set that moved is recomputed by one

@@ -57,6 +57,7 @@ SIGNATURES = {
     "ddm_write_async": (_i, [_vp, _u32, _u32, _vp, _u64, _vp, _vp, _vp]),
     "ddm_pair_offsets_async": (_i, [_vp, _vp, _u32, _vp, _vp]),
     "ddm_match_moved": (_i, [_vp, _vp, _vp, _u32, _vp, _u32, _vp, _u64, _vp, _vp]),
+    "ddm_plan_stats": (_i, [_vp, _vp]),
     "ddm_attach": (_i, [_vp, _vp]),
     "ddm_write": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
@@ -216,6 +217,13 @@ def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, e
     cap = 0 if pairs is None else pairs.shape[0]
     _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, _ptr(k_dev),
                                  _ptr(err_dev), _stream(stream)), "ddm_write_async")
+
+
+def ddm_plan_stats(ctx: int) -> int:
+    """(query, leaf) tests made by the last count pass that returned."""
+    v = ctypes.c_uint64(0)
+    _check(lib().ddm_plan_stats(ctx, ctypes.byref(v)), "ddm_plan_stats")
+    return v.value
 
 
 def ddm_match_moved(ctx: int, lo, hi, ids, pairs, flags: int = DDM_CLOSED, stream=None) -> int:

@@ -64,6 +64,7 @@ struct ddm_ctx {
   bool built = false;
   bool attached = false;        // tree borrowed from another context (ddm_attach)
   bool swapped = false;         // one-shot call with DDM_SWAP_ROLES: tree over the updates
+  uint64_t last_tests = 0;      // (query, leaf) tests of the last count pass read back
   TreeView tree{};
   bool planned = false;
   const float* ulo = nullptr;
@@ -383,7 +384,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
                            s));
     if (c->tree.n > 0) {
       DDM_CUDA(launch_count(c->tree, query_view(c), c->bv, flags, counts, counts_pos, c->arena,
-                            static_cast<uint32_t*>(c->work.p), packet_sms(c), s));
+                            static_cast<uint32_t*>(c->work.p), c->st_dev, packet_sms(c), s));
     } else {
       DDM_CUDA(cudaMemsetAsync(counts, 0, sizeof(uint32_t) * m, s));
       DDM_CUDA(cudaMemsetAsync(counts_pos, 0, sizeof(uint32_t) * m, s));
@@ -592,6 +593,7 @@ int ddm_plan(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_
     DDM_CUDA(cudaMemcpyAsync(offsets, c->offsets.p, sizeof(unsigned long long) * ((size_t)m + 1),
                              cudaMemcpyDeviceToDevice, s));
   DDM_TRY(sync_status(c, s));
+  c->last_tests = c->st_host->tests;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   if (rc != DDM_OK) c->planned = false;
@@ -658,6 +660,12 @@ int ddm_write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, u
   return DDM_OK;
 }
 
+int ddm_plan_stats(ddm_ctx* c, uint64_t* leaf_tests) {
+  if (!c || !leaf_tests) return DDM_ERR_ARG;
+  *leaf_tests = c->last_tests;
+  return DDM_OK;
+}
+
 int ddm_match_moved(ddm_ctx* c, const float* lo, const float* hi, uint32_t k, const uint32_t* ids,
                     uint32_t flags, ddm_pair* pairs, uint64_t capacity, uint64_t* k_out,
                     void* stream) {
@@ -677,6 +685,7 @@ int ddm_match_moved(ddm_ctx* c, const float* lo, const float* hi, uint32_t k, co
   c->swapped = was;
   DDM_TRY(wrc);
   DDM_TRY(sync_status(c, s));
+  c->last_tests = c->st_host->tests;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   if (rc != DDM_OK) c->planned = false;
@@ -768,6 +777,7 @@ static int match_impl(ddm_ctx* c, int d, const float* ulo, const float* uhi, uin
   DDM_TRY(plan_async(c, ulo, uhi, m, flags & DDM_OPEN, write, s));
   if (write) DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
   DDM_TRY(sync_status(c, s));
+  c->last_tests = c->st_host->tests;
   if (k_out) *k_out = c->st_host->K;
   const int rc = status_code(*c->st_host);
   // a swapped problem's tree and plan are not the caller's sets: no staged use
@@ -833,6 +843,7 @@ static int batch_impl(ddm_ctx* c, int d, uint32_t count, const float* ulo, const
   c->built = c->planned = false;
   if (!sync) return DDM_OK;
   DDM_TRY(sync_status(c, s));
+  c->last_tests = c->st_host->tests;
   if (k_out) *k_out = c->st_host->K;
   return status_code(*c->st_host);
 }

@@ -27,6 +27,7 @@ struct Status {
   unsigned int err;        // kErr* bits
   unsigned int pad;
   unsigned long long aux;  // call-specific (chunk end, ...)
+  unsigned long long tests;  // count pass: (query, leaf) tests, 32 subscriptions each
 };
 
 // Read-only view of a built tree, passed to kernels by value.
@@ -208,7 +209,8 @@ __device__ __forceinline__ bool records_complete(const RecordArena& ra) {
 // default of 8 CTAs of 256 threads per SM (tuning knob).
 cudaError_t launch_count(const TreeView& t, const QueryView& q, const BatchView& bv,
                          uint32_t flags, uint32_t* counts, uint32_t* counts_pos,
-                         const RecordArena& ra, uint32_t* work, int sms, cudaStream_t s);
+                         const RecordArena& ra, uint32_t* work, Status* st, int sms,
+                         cudaStream_t s);
 // Walking write pass; it does nothing when `ra` holds complete records (the
 // replay kernel, launched next to it, writes the pairs then).
 cudaError_t launch_write(const TreeView& t, const QueryView& q, const BatchView& bv,

@@ -146,7 +146,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
       if (a < d)
         s_q[wib][lane][k2] = make_float4(ql[a], qh[a], b < d ? ql[b] : 0.f, b < d ? qh[b] : 0.f);
     }
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, ntests = 0;
     unsigned long long out = 0;
     if (WRITE && valid) out = w.start[w.by_pos ? pos : Q] - base0;
     __syncwarp();
@@ -191,6 +191,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
         }
         uint32_t qm = __ballot_sync(0xffffffffu, qok);
         if (qm == 0u) continue;
+        if (!WRITE) ntests += __popc(qm);
         const uint32_t i = (g1 + cl) * 32u + lane;
         const bool iv = i < n;
         float2 ev[DM];
@@ -382,6 +383,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
       counts[Q] = cnt;
       if (counts_pos) counts_pos[pos] = cnt;
     }
+    if (!WRITE && st && lane == 0 && ntests) atomicAdd(&st->tests, (unsigned long long)ntests);
     if (recording && lane == 0) {
       if (rec_write) {
         if (cur_blk == kNoBlock) {
@@ -620,9 +622,10 @@ __global__ void k_gather_offsets(const unsigned long long* __restrict__ offsets,
 
 cudaError_t launch_count(const TreeView& t, const QueryView& q, const BatchView& bv,
                          uint32_t flags, uint32_t* counts, uint32_t* counts_pos,
-                         const RecordArena& ra, uint32_t* work, int sms, cudaStream_t s) {
+                         const RecordArena& ra, uint32_t* work, Status* st, int sms,
+                         cudaStream_t s) {
   WriteView w{};
-  return launch_packets<false>(t, q, bv, flags, counts, counts_pos, ra, w, work, nullptr, sms, s);
+  return launch_packets<false>(t, q, bv, flags, counts, counts_pos, ra, w, work, st, sms, s);
 }
 
 cudaError_t launch_write(const TreeView& t, const QueryView& q, const BatchView& bv,

@@ -403,3 +403,17 @@ def test_swap_roles_limits(ctx):
     with pytest.raises(ddm.DDMError) as e:
         ddm.ddm_plan(ctx, U[0], U[1], flags=ddm.DDM_SWAP_ROLES)
     assert e.value.code in (ddm.DDM_ERR_ARG, ddm.DDM_ERR_STATE)
+
+
+def test_plan_stats_bounds(ctx):
+    """ddm_plan_stats: every pair comes from a (query, leaf) test (<= 32 per
+    test), and no query tests more leaves than the tree has."""
+    import math
+    for d, (n, m) in ((1, (5000, 4000)), (3, (20000, 9000))):
+        arrays = W.uniform_fixed_length(n, m, d, 50.0, seed=11)
+        U = to_dev(arrays)
+        K = ddm.ddm_count(ctx, *U)
+        t = ddm.ddm_plan_stats(ctx)
+        assert K <= 32 * t
+        assert t <= m * math.ceil(n / 32)
+        assert t > 0
