@@ -126,11 +126,58 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
+def _device_tensor(t, what: str):
+    """Kernels read these arrays directly: a host (pageable) pointer would
+    fault the GPU, so only CUDA tensors (or pinned host tensors, which the
+    device can address) pass."""
+    if not (getattr(t, "is_cuda", False) or (hasattr(t, "is_pinned") and t.is_pinned())):
+        raise ValueError(f"{what} must be a CUDA tensor (or pinned host memory)")
+    if not t.is_contiguous():
+        raise ValueError(f"{what} must be contiguous")
+
+
+def _arr(t, what: str, itemsize: int, n: Optional[int] = None):
+    """Pointer of an optional device array argument (None passes NULL):
+    device-addressable, contiguous, `itemsize`-byte elements, at least `n`."""
+    if t is None:
+        return None
+    _device_tensor(t, what)
+    if t.element_size() != itemsize:
+        raise TypeError(f"{what} must hold {itemsize}-byte elements")
+    if n is not None and t.numel() < n:
+        raise ValueError(f"{what} needs at least {n} entries")
+    return t.data_ptr()
+
+
 def _set(lo, hi) -> Tuple[int, int, int, int]:
+    import torch
+    if lo.dim() != 2 or hi.shape != lo.shape:
+        raise ValueError("lo and hi must be (d, count) tensors of the same shape")
+    if lo.dtype != torch.float32 or hi.dtype != torch.float32:
+        raise TypeError("coordinates must be float32")
+    _device_tensor(lo, "lo")
+    _device_tensor(hi, "hi")
     d, c = lo.shape
-    assert hi.shape == lo.shape, "lo and hi must have the same shape"
-    assert lo.is_contiguous() and hi.is_contiguous(), "coordinates must be C-contiguous"
     return d, _ptr(lo), _ptr(hi), c
+
+
+def _two_sets(upd_lo, upd_hi, sub_lo, sub_hi):
+    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d2, sl, sh, n = _set(sub_lo, sub_hi)
+    if d != d2:
+        raise ValueError(f"update and subscription sets have {d} and {d2} dimensions")
+    return d, ul, uh, m, sl, sh, n
+
+
+def _pairs(pairs) -> int:
+    """Capacity of a pair buffer: an int32 (capacity, 2) tensor."""
+    import torch
+    if pairs is None:
+        return 0
+    if pairs.dtype != torch.int32 or pairs.dim() != 2 or pairs.shape[1] != 2:
+        raise TypeError("pairs must be an int32 tensor of shape (capacity, 2)")
+    _device_tensor(pairs, "pairs")
+    return pairs.shape[0]
 
 
 def _check(rc: int, where: str, k: Optional[int] = None):
@@ -150,9 +197,7 @@ def ddm_destroy(ctx: int) -> None:
 
 def ddm_count(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, flags: int = DDM_CLOSED,
               stream=None) -> int:
-    d, ul, uh, m = _set(upd_lo, upd_hi)
-    d2, sl, sh, n = _set(sub_lo, sub_hi)
-    assert d == d2
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_count(ctx, d, ul, uh, m, sl, sh, n, flags, ctypes.byref(k), _stream(stream))
     _check(rc, "ddm_count", k.value)
@@ -161,10 +206,8 @@ def ddm_count(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, flags: int = DDM_CLOSED,
 
 def ddm_match(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, pairs, flags: int = DDM_CLOSED,
               stream=None) -> int:
-    d, ul, uh, m = _set(upd_lo, upd_hi)
-    d2, sl, sh, n = _set(sub_lo, sub_hi)
-    assert d == d2
-    cap = 0 if pairs is None else pairs.shape[0]
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
+    cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_match(ctx, d, ul, uh, m, sl, sh, n, flags, _ptr(pairs), cap, ctypes.byref(k),
                          _stream(stream))
@@ -174,10 +217,8 @@ def ddm_match(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, pairs, flags: int = DDM_
 
 def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, upd_end: int,
                     pairs, flags: int = DDM_CLOSED, stream=None) -> int:
-    d, ul, uh, m = _set(upd_lo, upd_hi)
-    d2, sl, sh, n = _set(sub_lo, sub_hi)
-    assert d == d2
-    cap = 0 if pairs is None else pairs.shape[0]
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
+    cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_match_range(ctx, d, ul, uh, m, sl, sh, n, upd_begin, upd_end, flags,
                                _ptr(pairs), cap, ctypes.byref(k), _stream(stream))
@@ -191,7 +232,10 @@ def ddm_build(ctx: int, sub_lo, sub_hi, stream=None) -> None:
 
 
 def ddm_refit(ctx: int, sub_lo, sub_hi, stream=None) -> None:
-    _check(lib().ddm_refit(ctx, _ptr(sub_lo), _ptr(sub_hi), _stream(stream)), "ddm_refit")
+    sl = sh = None
+    if sub_lo is not None or sub_hi is not None:
+        _, sl, sh, _ = _set(sub_lo, sub_hi)
+    _check(lib().ddm_refit(ctx, sl, sh, _stream(stream)), "ddm_refit")
 
 
 def ddm_attach(ctx: int, src: int) -> None:
@@ -202,7 +246,8 @@ def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
              stream=None) -> int:
     d, ul, uh, m = _set(upd_lo, upd_hi)
     k = ctypes.c_uint64(0)
-    rc = lib().ddm_plan(ctx, ul, uh, m, flags, _ptr(offsets), ctypes.byref(k), _stream(stream))
+    rc = lib().ddm_plan(ctx, ul, uh, m, flags, _arr(offsets, "offsets", 8, m + 1), ctypes.byref(k),
+                        _stream(stream))
     _check(rc, "ddm_plan", k.value)
     return k.value
 
@@ -214,9 +259,10 @@ def ddm_plan_async(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, stream=Non
 
 def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, err_dev=None,
                     stream=None) -> None:
-    cap = 0 if pairs is None else pairs.shape[0]
-    _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, _ptr(k_dev),
-                                 _ptr(err_dev), _stream(stream)), "ddm_write_async")
+    cap = _pairs(pairs)
+    kd, ed = _arr(k_dev, "k_dev", 8, 1), _arr(err_dev, "err_dev", 4, 1)
+    _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, kd, ed,
+                                 _stream(stream)), "ddm_write_async")
 
 
 def ddm_plan_stats(ctx: int) -> int:
@@ -233,9 +279,9 @@ def ddm_match_moved(ctx: int, lo, hi, ids, pairs, flags: int = DDM_CLOSED, strea
     d, l, h, k = _set(lo, hi)
     if ids is not None and ids.shape[0] != k:
         raise ValueError("ids needs one entry per moved extent")
-    cap = 0 if pairs is None else pairs.shape[0]
+    cap = _pairs(pairs)
     kk = ctypes.c_uint64(0)
-    rc = lib().ddm_match_moved(ctx, l, h, k, _ptr(ids), flags, _ptr(pairs), cap,
+    rc = lib().ddm_match_moved(ctx, l, h, k, _arr(ids, "ids", 4, k), flags, _ptr(pairs), cap,
                                ctypes.byref(kk), _stream(stream))
     _check(rc, "ddm_match_moved", kk.value)
     return kk.value
@@ -247,12 +293,13 @@ def ddm_pair_offsets_async(ctx: int, upd_off, pair_off, stream=None) -> None:
     count = upd_off.shape[0] - 1
     if count < 0 or pair_off.shape[0] < count + 1:
         raise ValueError("upd_off and pair_off need count + 1 entries")
-    _check(lib().ddm_pair_offsets_async(ctx, _ptr(upd_off), count, _ptr(pair_off), _stream(stream)),
+    _check(lib().ddm_pair_offsets_async(ctx, _arr(upd_off, "upd_off", 8, count + 1), count,
+                                        _arr(pair_off, "pair_off", 8, count + 1), _stream(stream)),
            "ddm_pair_offsets_async")
 
 
 def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int:
-    cap = 0 if pairs is None else pairs.shape[0]
+    cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write(ctx, upd_begin, upd_end, _ptr(pairs), cap, ctypes.byref(k),
                          _stream(stream))
@@ -268,12 +315,12 @@ def ddm_chunk_end(ctx: int, upd_begin: int, capacity: int, stream=None) -> int:
 
 
 def ddm_plan_order(ctx: int, order=None, order_offsets=None, stream=None) -> None:
-    _check(lib().ddm_plan_order(ctx, _ptr(order), _ptr(order_offsets), _stream(stream)),
-           "ddm_plan_order")
+    o, oo = _arr(order, "order", 4), _arr(order_offsets, "order_offsets", 8)
+    _check(lib().ddm_plan_order(ctx, o, oo, _stream(stream)), "ddm_plan_order")
 
 
 def ddm_write_ordered(ctx: int, pos_begin: int, pos_end: int, pairs, stream=None) -> int:
-    cap = 0 if pairs is None else pairs.shape[0]
+    cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write_ordered(ctx, pos_begin, pos_end, _ptr(pairs), cap, ctypes.byref(k),
                                  _stream(stream))
@@ -297,7 +344,8 @@ def ddm_tree_shape(ctx: int) -> Tuple[int, Sequence[int], int]:
 
 
 def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=None) -> None:
-    _check(lib().ddm_tree_export(ctx, _ptr(order), _ptr(node_lo), _ptr(node_hi),
+    _check(lib().ddm_tree_export(ctx, _arr(order, "order", 4), _arr(node_lo, "node_lo", 4),
+                                 _arr(node_hi, "node_hi", 4),
                                  _stream(stream)), "ddm_tree_export")
 
 
@@ -320,7 +368,8 @@ def ddm_debug_launch_count() -> int:
 def ddm_scan_counts_noalloc(counts, offsets, stream=None) -> None:
     """Offsets (int64 device tensor, m + 1) from per-update counts (int32
     device tensor, m) without any allocation; see include/ddm.h."""
-    _check(lib().ddm_scan_counts_noalloc(_ptr(counts), counts.shape[0], _ptr(offsets),
+    _check(lib().ddm_scan_counts_noalloc(_arr(counts, "counts", 4), counts.shape[0],
+                                         _arr(offsets, "offsets", 8, counts.shape[0] + 1),
                                          _stream(stream)), "ddm_scan_counts_noalloc")
 
 
@@ -328,15 +377,15 @@ def ddm_batch_match(ctx: int, upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub_off, 
                     pair_off=None, flags: int = DDM_CLOSED, stream=None) -> int:
     """Batched instances (see include/ddm.h).  upd_off / sub_off: int64 device
     tensors of count + 1 offsets; pairs: int32 device tensor (capacity, 2)."""
-    d, ul, uh, m = _set(upd_lo, upd_hi)
-    d2, sl, sh, n = _set(sub_lo, sub_hi)
-    assert d == d2
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
     count = upd_off.shape[0] - 1
-    cap = 0 if pairs is None else pairs.shape[0]
+    cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
-    rc = lib().ddm_batch_match(ctx, d, count, ul, uh, _ptr(upd_off), m, sl, sh, _ptr(sub_off), n,
-                               flags, _ptr(pairs), cap, _ptr(pair_off), ctypes.byref(k),
-                               _stream(stream))
+    uo = _arr(upd_off, "upd_off", 8, count + 1)
+    so = _arr(sub_off, "sub_off", 8, count + 1)
+    po = _arr(pair_off, "pair_off", 8, count + 1)
+    rc = lib().ddm_batch_match(ctx, d, count, ul, uh, uo, m, sl, sh, so, n, flags, _ptr(pairs), cap,
+                               po, ctypes.byref(k), _stream(stream))
     _check(rc, "ddm_batch_match", k.value)
     return k.value
 
@@ -345,12 +394,13 @@ def ddm_batch_match_async(ctx: int, upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub
                           pair_off=None, k_dev=None, err_dev=None, flags: int = DDM_CLOSED,
                           stream=None) -> None:
     """Host-synchronisation-free batched match (capturable in a CUDA graph)."""
-    d, ul, uh, m = _set(upd_lo, upd_hi)
-    d2, sl, sh, n = _set(sub_lo, sub_hi)
-    assert d == d2
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
     count = upd_off.shape[0] - 1
-    cap = 0 if pairs is None else pairs.shape[0]
-    rc = lib().ddm_batch_match_async(ctx, d, count, ul, uh, _ptr(upd_off), m, sl, sh,
-                                     _ptr(sub_off), n, flags, _ptr(pairs), cap, _ptr(pair_off),
-                                     _ptr(k_dev), _ptr(err_dev), _stream(stream))
+    cap = _pairs(pairs)
+    uo = _arr(upd_off, "upd_off", 8, count + 1)
+    so = _arr(sub_off, "sub_off", 8, count + 1)
+    po = _arr(pair_off, "pair_off", 8, count + 1)
+    rc = lib().ddm_batch_match_async(ctx, d, count, ul, uh, uo, m, sl, sh, so, n, flags,
+                                     _ptr(pairs), cap, po, _arr(k_dev, "k_dev", 8, 1),
+                                     _arr(err_dev, "err_dev", 4, 1), _stream(stream))
     _check(rc, "ddm_batch_match_async")

@@ -76,3 +76,20 @@ def test_product_path_does_not_import_oracle():
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 assert not pat.search(open(os.path.join(root, f)).read()), f
+
+
+def test_binding_rejects_host_and_mistyped_arrays():
+    """The kernels read coordinates directly: the binding refuses pageable
+    host tensors, wrong dtypes and mismatched shapes before any library call
+    (no GPU needed)."""
+    import torch
+    lo = torch.zeros((2, 8), dtype=torch.float32)
+    hi = torch.ones((2, 8), dtype=torch.float32)
+    with pytest.raises(ValueError):
+        ddm.ddm_count(0, lo, hi, lo, hi)                        # host memory
+    with pytest.raises(TypeError):
+        ddm.ddm_count(0, lo.double(), hi.double(), lo, hi)      # float64
+    with pytest.raises(ValueError):
+        ddm.ddm_count(0, lo, hi[:, :4], lo, hi)                 # shapes differ
+    with pytest.raises(ValueError):
+        ddm.ddm_count(0, lo, hi, lo[:1], hi[:1])                # d differs
