@@ -17,8 +17,13 @@
  * dimension with Intersect-1D.  On the GPU the tree is implicit (32 children
  * per node), keeps the subtree bounds for every dimension, and refines the
  * order near the leaves by the lower bounds of dimensions 1..d-1 inside
- * aligned groups of the dimension-0 order.  Queries are independent
- * (Section IV, "Parallelizing ITM") and run 32 per warp.
+ * aligned groups of the dimension-0 order; for d >= 2 the subscriptions are
+ * first grouped by size class (the binary exponent of their largest side),
+ * each class ordered and refined on its own, so that long extents do not
+ * widen the boxes of short ones.  Any order gives the same pairs (Section
+ * IV allows any interval tree); d = 1 keeps the paper's order exactly.
+ * Queries are independent (Section IV, "Parallelizing ITM") and run 32 per
+ * warp.
  *
  * Conventions shared by every call:
  *  - Coordinates are float32 in structure-of-arrays layout: for a set of c

@@ -55,6 +55,8 @@ struct ddm_ctx {
   RecordArena arena{};          // arena of the current plan (max_blocks 0 = none)
   // batched instances
   DevBuf inst_s, inst_u, bglog2, bngroups, bgbase;
+  // size classes of the tree order (d >= 2)
+  DevBuf cls_hist, cls_off;
   BatchView bv{};               // count 0 = single problem
   // tuning knobs (ddm_set_tuning)
   int str_shift = 0;            // added to the re-sort group exponents
@@ -231,6 +233,45 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
   return DDM_OK;
 }
 
+// Tree order for d >= 2: sort by (size class, lower bound), then refine
+// each class by the sort-tile-recursive re-sorts of its own size (the
+// per-instance machinery of batched sets, with the classes as instances).
+int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt, int* cur,
+                      cudaStream_t s) {
+  constexpr uint32_t kClasses = 256;
+  *cur = 0;
+  DDM_TRY(ensure_sort(c, cnt));
+  DDM_TRY(ensure(c, c->cls_hist, sizeof(uint32_t) * kClasses));
+  DDM_TRY(ensure(c, c->cls_off, sizeof(unsigned long long) * (kClasses + 1)));
+  DDM_TRY(ensure(c, c->inst_s, sizeof(uint32_t) * cnt));
+  DDM_TRY(ensure(c, c->bglog2, sizeof(int) * kClasses));
+  DDM_TRY(ensure(c, c->bngroups, sizeof(uint32_t) * kClasses));
+  DDM_TRY(ensure(c, c->bgbase, sizeof(unsigned long long) * (kClasses + 1)));
+  DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * 4));
+  auto* hist = static_cast<uint32_t*>(c->cls_hist.p);
+  auto* off = static_cast<unsigned long long*>(c->cls_off.p);
+  auto* inst = static_cast<uint32_t*>(c->inst_s.p);
+  auto* sums = static_cast<unsigned long long*>(c->sums.p);
+  DDM_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kClasses, s));
+  DDM_CUDA(launch_validate_class(d, lo, hi, cnt, static_cast<unsigned long long*>(c->keys[0].p),
+                                 static_cast<uint32_t*>(c->vals[0].p), hist, c->st_dev, c->sms, s));
+  DDM_TRY(sort_pass(c, cnt, 8, cur, s));
+  DDM_CUDA(launch_scan(hist, kClasses, off, sums, nullptr, s));
+  DDM_CUDA(launch_fill_inst(off, kClasses, inst, s));
+  for (int k = 1; k < d; ++k) {
+    auto* gl = static_cast<int*>(c->bglog2.p);
+    auto* ng = static_cast<uint32_t*>(c->bngroups.p);
+    auto* gb = static_cast<unsigned long long*>(c->bgbase.p);
+    DDM_CUDA(launch_batch_groups(off, kClasses, d, k, c->str_shift, gl, ng, s));
+    DDM_CUDA(launch_scan(ng, kClasses, gb, sums, nullptr, s));
+    DDM_CUDA(launch_rekey_batch(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt,
+                                cnt, inst, off, gl, gb,
+                                static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
+    DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(cnt), cur, s));  // at most cnt groups
+  }
+  return DDM_OK;
+}
+
 int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt, bool tree,
               int* cur, cudaStream_t s) {
   *cur = 0;
@@ -276,6 +317,8 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
   int cur = 0;
   if (bs)
     DDM_TRY(order_set_batch(c, d, slo, shi, n, *bs, &cur, s));
+  else if (d >= 2)
+    DDM_TRY(order_set_classes(c, d, slo, shi, n, &cur, s));
   else
     DDM_TRY(order_set(c, d, slo, shi, n, true, &cur, s));
   t.e = static_cast<const float2*>(c->e.p);
@@ -534,7 +577,7 @@ int ddm_destroy(ddm_ctx* c) {
                     &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
                     &c->blk_pkt, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
                     &c->blk_list, &c->blk_counter, &c->inst_s, &c->inst_u, &c->bglog2,
-                    &c->bngroups, &c->bgbase})
+                    &c->bngroups, &c->bgbase, &c->cls_hist, &c->cls_off})
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);

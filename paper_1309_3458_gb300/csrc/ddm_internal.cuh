@@ -123,6 +123,11 @@ cudaError_t launch_validate(int d, const float* lo, const float* hi, uint32_t cn
 cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, int glog2,
                          unsigned long long* keys, int sms, cudaStream_t s);
 // Batched sets: inst[i] = instance owning position i (off has count+1 entries).
+// Validation and class-major tree keys for d >= 2; hist[256] (zeroed by the
+// caller) receives the number of extents of each size class.
+cudaError_t launch_validate_class(int d, const float* lo, const float* hi, uint32_t cnt,
+                                  unsigned long long* keys, uint32_t* vals, uint32_t* hist,
+                                  Status* st, int sms, cudaStream_t s);
 cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t* inst,
                              cudaStream_t s);
 // Batched validation + keys: keys[i] = inst[i] << 32 | key(lo0[i]).

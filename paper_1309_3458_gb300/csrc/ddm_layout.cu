@@ -66,6 +66,43 @@ k_gather(int d, const uint32_t* __restrict__ vals, const float* __restrict__ lo,
   }
 }
 
+// Validation plus the first sort key of the tree order for d >= 2: the size
+// class of the extent -- the binary exponent of its largest side (the float
+// exponent field) -- then the dimension-0 lower bound and, in the low 24
+// bits, the top of the upper bound.  Sorting by class first keeps extents of
+// similar size together, so that one long extent does not widen the boxes
+// of a leaf of short ones; the order is a heuristic (node bounds come from
+// the coordinates whatever the order).  hist[class] counts the extents.
+__global__ void __launch_bounds__(kThreads)
+k_validate_class(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
+                 unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
+                 uint32_t* __restrict__ hist, Status* __restrict__ st) {
+  __shared__ uint32_t s_h[256];
+  for (int i = threadIdx.x; i < 256; i += blockDim.x) s_h[i] = 0u;
+  __syncthreads();
+  bool bad = false;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
+    float side = 0.0f;
+    for (int k = 0; k < d; ++k) {
+      const float a = __ldg(lo + (size_t)k * cnt + i);
+      const float b = __ldg(hi + (size_t)k * cnt + i);
+      bad |= !(a <= b);
+      side = fmaxf(side, b - a);
+    }
+    const uint32_t cls = (__float_as_uint(side) >> 23) & 0xffu;
+    keys[i] = ((unsigned long long)cls << 56) |
+              ((unsigned long long)float_key(__ldg(lo + i)) << 24) |
+              (unsigned long long)(float_key(__ldg(hi + i)) >> 8);
+    vals[i] = i;
+    atomicAdd(&s_h[cls], 1u);
+  }
+  if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->err, kErrExtent);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
+}
+
 // Batched sets: one CTA per instance marks its positions.
 __global__ void k_fill_inst(const unsigned long long* __restrict__ off, uint32_t* __restrict__ inst) {
   const unsigned long long b = off[blockIdx.x], e = off[blockIdx.x + 1];
@@ -140,6 +177,15 @@ cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const fl
                           uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
   k_gather<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, vals, lo, hi, cnt, qe, qid);
+  note_launches(1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_class(int d, const float* lo, const float* hi, uint32_t cnt,
+                                  unsigned long long* keys, uint32_t* vals, uint32_t* hist,
+                                  Status* st, int sms, cudaStream_t s) {
+  if (cnt == 0) return cudaSuccess;
+  k_validate_class<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, keys, vals, hist, st);
   note_launches(1);
   return cudaGetLastError();
 }

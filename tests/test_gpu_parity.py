@@ -12,6 +12,8 @@ whole list is compared element by element.  For d > 1 the GPU tree refines
 the order near the leaves, so the subscription column is compared as a set
 per update, and the order is checked against the tree's exported order.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -161,13 +163,50 @@ def test_tree_order_and_node_bounds(ctx):
             mx = np.concatenate([hi, np.full(pad, -np.inf, np.float32)]).reshape(c, span).max(1)
             assert np.array_equal(nlo[k, pos:pos + c], mn) and np.array_equal(nhi[k, pos:pos + c], mx)
             pos += c
-    # Re-sort groups are aligned powers of two smaller than n, so every
-    # aligned block of 2^16 positions holds exactly the extents that the
-    # paper's dimension-0 (lower, upper, id) order puts there.
-    want, _ = oracle.tree_order(arrays[2][0], arrays[3][0])
-    blk = 1 << 16
-    for b in range(0, n, blk):
-        assert np.array_equal(np.sort(order[b:b + blk]), np.sort(want[b:b + blk]))
+    # Order for d >= 2: size classes ascending (the binary exponent of each
+    # extent's largest side), and inside a class the dimension-0 lower bounds
+    # ascend from one re-sort group to the next (aligned powers of two counted
+    # from the class's first position).
+    side = (arrays[3] - arrays[2]).max(axis=0)          # float32, as on the device
+    cls = (side.view(np.uint32) >> 23) & 0xff
+    c_ord = cls[order]
+    assert (np.diff(c_ord.astype(np.int64)) >= 0).all()
+    lo0 = arrays[2][0][order]
+    for c in np.unique(c_ord):
+        pos = np.nonzero(c_ord == c)[0]
+        start, cnt = int(pos[0]), len(pos)
+        G = 1 << resort_bits(cnt, 3)
+        seg = lo0[start:start + cnt]
+        nb = -(-cnt // G)
+        pad = nb * G - cnt
+        bmax = np.concatenate([seg, np.full(pad, -np.inf, np.float32)]).reshape(nb, G).max(1)
+        bmin = np.concatenate([seg, np.full(pad, np.inf, np.float32)]).reshape(nb, G).min(1)
+        assert (bmax[:-1] <= bmin[1:]).all()
+
+
+def str_group_log2(n, d, k):
+    """Re-sort group exponent for dimension k of a set of n extents: groups of
+    32 * nb^((d-k)/d) positions (nb = n/32 leaves, sort-tile-recursive
+    packing), rounded to a power of two; 0 = no re-sort."""
+    if n < 64:
+        return 0
+    nb = (n + 31) // 32
+    g = int(math.floor(math.log2(32.0 * nb ** ((d - k) / d)) + 0.5))
+    return 0 if g < 6 or (1 << g) >= n else g
+
+
+def resort_bits(n, d):
+    """Largest re-sort group exponent over dimensions 1..d-1 (each strictly
+    smaller than the ones before it, else none)."""
+    best = 0
+    for k in range(1, d):
+        g = str_group_log2(n, d, k)
+        for j in range(1, k):
+            gp = str_group_log2(n, d, j)
+            if gp > 0 and g >= gp:
+                g = 0
+        best = max(best, g)
+    return best
 
 
 def test_tree_order_d1_is_paper_order(ctx):
