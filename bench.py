@@ -569,7 +569,9 @@ def main():
     # Inputs are copied from pinned host memory every step and every pair is
     # copied back to pinned host memory.  The device pair buffer is split in
     # two halves: while one half's pairs travel to the host on a copy stream,
-    # the next chunk is written into the other half.
+    # the next chunk is written into the other half.  Two contexts alternate
+    # between steps, so that a step's build and count run while the previous
+    # step's last pairs are still being copied out.
     e2e = None
     if not args.no_e2e:
         host = [torch.from_numpy(a).pin_memory() for a in arrays]
@@ -580,40 +582,48 @@ def main():
         bufs = (pairs[:half], pairs[half:2 * half])
         copy_stream = torch.cuda.Stream()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
+        ctxs = (ctx, ddm.ddm_create(local))
+        chunk_no = [0]
 
-        def e2e_step():
-            for t_dev, t_host in zip(dev, host):
-                t_dev.copy_(t_host, non_blocking=True)
-            ddm.ddm_build(ctx, dev[2], dev[3])
-            Ke = ddm.ddm_plan(ctx, dev[0], dev[1])
-            b, i = 0, 0
-            while b < m:
-                e = ddm.ddm_chunk_end_ordered(ctx, b, half)
-                buf = bufs[i % 2]
-                stream.wait_event(copied[i % 2])      # that half's previous pairs are out
-                k = ddm.ddm_write_ordered(ctx, b, e, buf)
-                written = torch.cuda.Event()
-                written.record(stream)
-                copy_stream.wait_event(written)
-                with torch.cuda.stream(copy_stream):
-                    o = 0
-                    while o < k:
-                        c = min(stage.shape[0], k - o)
-                        stage[:c].copy_(buf[o:o + c], non_blocking=True)
-                        o += c
-                    copied[i % 2].record(copy_stream)
-                b, i = e, i + 1
+        def e2e_run(nsteps):
+            Ke = 0
+            for st in range(nsteps):
+                c = ctxs[st % 2]
+                for t_dev, t_host in zip(dev, host):
+                    t_dev.copy_(t_host, non_blocking=True)
+                ddm.ddm_build(c, dev[2], dev[3])
+                Ke = ddm.ddm_plan(c, dev[0], dev[1])
+                b = 0
+                while b < m:
+                    e = ddm.ddm_chunk_end_ordered(c, b, half)
+                    i = chunk_no[0]
+                    buf = bufs[i % 2]
+                    stream.wait_event(copied[i % 2])      # that half's previous pairs are out
+                    k = ddm.ddm_write_ordered(c, b, e, buf)
+                    written = torch.cuda.Event()
+                    written.record(stream)
+                    copy_stream.wait_event(written)
+                    with torch.cuda.stream(copy_stream):
+                        o = 0
+                        while o < k:
+                            n_c = min(stage.shape[0], k - o)
+                            stage[:n_c].copy_(buf[o:o + n_c], non_blocking=True)
+                            o += n_c
+                        copied[i % 2].record(copy_stream)
+                    b, chunk_no[0] = e, i + 1
             stream.wait_stream(copy_stream)
             torch.cuda.synchronize()
             return Ke
 
-        e2e_step()
+        for _ in range(2):   # size the second context's workspace and record arena
+            ddm.ddm_build(ctxs[1], dev[2], dev[3])
+            ddm.ddm_plan(ctxs[1], dev[0], dev[1])
+        e2e_run(1)
         barrier()
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(e2e_steps):
-            Ke = e2e_step()
+        Ke = e2e_run(e2e_steps)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
@@ -621,6 +631,7 @@ def main():
         e2e = {"value": Ke * e2e_steps / te * (world if world > 1 else 1), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * Ke),
                "steps": e2e_steps}
+        ddm.ddm_destroy(ctxs[1])
         del host, stage
 
     ddm.ddm_destroy(ctx)
