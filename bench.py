@@ -409,6 +409,45 @@ def count_roofline(leaf_tests, d, count_ms, steps):
             "peak_source": "unit counts x max SM clock"}
 
 
+def configs_section(skip: str, reps: int = 3):
+    """Every other named workload (the paper's Section V shapes: d = 1 at
+    N = 1e4, d = 1 and 2 at N = 1e6 for alpha = 0.01, 1, 100): one full
+    ddm_match each (build, count, write, pairs in a device buffer), median of
+    `reps` timed with CUDA events after one warm-up."""
+    import torch
+
+    import paper_1309_3458_gb300 as ddm
+    from paper_1309_3458_gb300 import workloads as W
+    ctx = ddm.ddm_create(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    out = []
+    try:
+        for name in W.CONFIGS:
+            if name == skip:
+                continue
+            U = [torch.from_numpy(x).cuda() for x in W.make(name)]
+            K = ddm.ddm_count(ctx, *U)
+            buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+            ddm.ddm_match(ctx, *U, buf)
+            ts = []
+            for _ in range(reps):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ddm.ddm_match(ctx, *U, buf)
+                e1.record(stream)
+                e1.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ts.sort()
+            ms = ts[len(ts) // 2]
+            out.append({"workload": name, "K": K, "ms": round(ms, 4),
+                        "pairs_per_s": K / (ms / 1e3) if ms > 0 else None,
+                        "queries_per_s": U[0].shape[1] / (ms / 1e3) if ms > 0 else None})
+            del buf, U
+    finally:
+        ddm.ddm_destroy(ctx)
+    return out
+
+
 def sweep_section(reps: int = 3):
     """The shape of the paper's Fig. 7 (Section V): d = 1 uniform workloads,
     N = n + m in {5e4, 1e5, 2.5e5, 5e5}, overlapping degree alpha in
@@ -649,9 +688,10 @@ def main():
         torch.cuda.empty_cache()
         serving = serving_section(args.serving_seconds)
 
-    sweep = None
+    sweep = others = None
     if not args.no_sweep and world == 1:
         sweep = sweep_section()
+        others = configs_section(args.config)
 
     cpu = None
     if not args.no_cpu and world == 1:
@@ -701,6 +741,7 @@ def main():
         "batched": batched,
         "serving": serving,
         "alpha_n_sweep": sweep,
+        "other_configs": others,
     }
     print(json.dumps(line), flush=True)
 

@@ -456,3 +456,34 @@ def test_plan_stats_bounds(ctx):
         assert K <= 32 * t
         assert t <= m * math.ceil(n / 32)
         assert t > 0
+
+
+@pytest.mark.parametrize("flags", [0, 1])
+def test_maximum_dimensions(ctx, flags):
+    """d = DDM_MAX_DIMS (8): the runtime-d kernels at their limit, ties and
+    touching faces in every dimension."""
+    for seed in range(4):
+        rng = np.random.default_rng(77 + seed)
+        n, m = (int(v) for v in rng.integers(1, 400, size=2))
+        check_exact(ctx, W.grid_random(n, m, 8, seed=seed, grid=3), flags)
+    check_exact(ctx, W.uniform_fixed_length(3000, 2000, 8, 5.0, seed=3), flags)
+
+
+def test_size_and_dimension_limits(ctx):
+    """Counts above DDM_MAX_EXTENTS and d outside 1..8 are refused on the
+    host, before any device work (the pointers are never read)."""
+    import ctypes
+    import torch
+    lib = ddm.lib()
+    lo = torch.zeros((2, 4), device="cuda")
+    k = ctypes.c_uint64(0)
+    p = lo.data_ptr()
+    big = 1073741824  # DDM_MAX_EXTENTS + 1
+    s = torch.cuda.current_stream().cuda_stream
+    assert lib.ddm_count(ctx, 2, p, p, big, p, p, 4, 0, ctypes.byref(k), s) == ddm.DDM_ERR_ARG
+    assert lib.ddm_count(ctx, 2, p, p, 4, p, p, big, 0, ctypes.byref(k), s) == ddm.DDM_ERR_ARG
+    assert lib.ddm_count(ctx, 9, p, p, 4, p, p, 4, 0, ctypes.byref(k), s) == ddm.DDM_ERR_ARG
+    assert lib.ddm_count(ctx, 0, p, p, 4, p, p, 4, 0, ctypes.byref(k), s) == ddm.DDM_ERR_ARG
+    assert lib.ddm_count(ctx, 2, p, p, 4, p, p, 4, 8, ctypes.byref(k), s) == ddm.DDM_ERR_ARG  # flag
+    # the context is still usable
+    check_exact(ctx, W.uniform_fixed_length(300, 200, 2, 10.0, seed=1))
