@@ -75,9 +75,12 @@ k_scan_sums(unsigned long long* __restrict__ sums, uint32_t tiles, unsigned long
   }
 }
 
+// ONE: a single tile (m <= kScanTile) scanned by one CTA with no tile sums;
+// it also writes the total to offsets[m] and st->K.
+template <bool ONE>
 __global__ void __launch_bounds__(kThreads)
 k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned long long* __restrict__ sums,
-             unsigned long long* __restrict__ offsets) {
+             unsigned long long* __restrict__ offsets, Status* __restrict__ st) {
   __shared__ uint32_t s_c[kScanTile];
   const size_t base = (size_t)blockIdx.x * kScanTile;
 #pragma unroll
@@ -91,7 +94,11 @@ k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned lon
 #pragma unroll
   for (int i = 0; i < kItems; ++i) local += s_c[threadIdx.x * kItems + i];
   unsigned long long tot;
-  unsigned long long run = sums[blockIdx.x] + block_excl_scan(local, &tot);
+  unsigned long long run = (ONE ? 0ull : sums[blockIdx.x]) + block_excl_scan(local, &tot);
+  if (ONE && threadIdx.x == 0) {
+    offsets[m] = tot;
+    if (st) st->K = tot;
+  }
   unsigned long long out[kItems];
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
@@ -164,9 +171,15 @@ cudaError_t launch_select(const uint32_t* qid, uint32_t m, uint32_t begin, uint3
 cudaError_t launch_scan(const uint32_t* counts, uint32_t m, unsigned long long* offsets,
                         unsigned long long* block_sums, Status* st, cudaStream_t s) {
   const uint32_t tiles = (m + kScanTile - 1) / kScanTile;
+  if (tiles == 1) {  // one CTA does it all
+    k_scan_tiles<true><<<1, kThreads, 0, s>>>(counts, m, block_sums, offsets, st);
+    note_launches(1);
+    return cudaGetLastError();
+  }
   if (tiles > 0) k_tile_sums<<<tiles, kThreads, 0, s>>>(counts, m, block_sums);
   k_scan_sums<<<1, kThreads, 0, s>>>(block_sums, tiles, offsets, m, st);
-  if (tiles > 0) k_scan_tiles<<<tiles, kThreads, 0, s>>>(counts, m, block_sums, offsets);
+  if (tiles > 0)
+    k_scan_tiles<false><<<tiles, kThreads, 0, s>>>(counts, m, block_sums, offsets, nullptr);
   note_launches(tiles > 0 ? 3u : 1u);
   return cudaGetLastError();
 }
@@ -237,7 +250,7 @@ extern "C" int ddm_scan_counts_noalloc(const uint32_t* counts, uint32_t m, uint6
   auto* off = reinterpret_cast<unsigned long long*>(offsets);
   if (tiles > 0) k_tile_sums<<<tiles, kThreads, 0, s>>>(counts, m, sums);
   k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, off, m, nullptr);
-  if (tiles > 0) k_scan_tiles<<<tiles, kThreads, 0, s>>>(counts, m, sums, off);
+  if (tiles > 0) k_scan_tiles<false><<<tiles, kThreads, 0, s>>>(counts, m, sums, off, nullptr);
   note_launches(tiles > 0 ? 3u : 1u);
   if (cudaGetLastError() != cudaSuccess) return DDM_ERR_CUDA;
   return DDM_OK;

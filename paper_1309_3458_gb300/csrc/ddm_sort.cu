@@ -212,6 +212,110 @@ k_onesweep(const unsigned long long* __restrict__ in_keys, const uint32_t* __res
   }
 }
 
+// Small arrays (n <= kSmallTile): one CTA of 512 threads runs every digit
+// pass in shared memory -- the same stable ranking as k_onesweep (warp match
+// + per-warp counters, warps in order), with the tile's own digit offsets in
+// place of the look-back -- so the whole sort is one launch.
+constexpr int kSmallThreads = 512;
+constexpr int kSmallWarps = kSmallThreads / 32;
+constexpr uint32_t kSmallTile = kSmallThreads * kItems;  // 8192
+
+struct SmallSortSmem {
+  uint32_t whist[kSmallWarps][kRadix];
+  uint32_t wtot[kRadix / 32];
+  uint32_t lstart[kRadix];
+  unsigned long long keys[kSmallTile];
+  uint32_t vals[kSmallTile];
+};
+
+__global__ void __launch_bounds__(kSmallThreads, 1)
+k_sort_small(const unsigned long long* __restrict__ in_keys, const uint32_t* __restrict__ in_vals,
+             unsigned long long* __restrict__ out_keys, uint32_t* __restrict__ out_vals,
+             uint32_t n, int passes) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  SmallSortSmem& sm = *reinterpret_cast<SmallSortSmem*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = lanemask_lt();
+  unsigned long long key[kItems];
+  uint32_t val[kItems], rank[kItems];
+  // item i of lane l in warp w is element w*512 + i*32 + l (input order)
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t local = warp * (kItems * 32) + i * 32 + lane;
+    key[i] = local < n ? in_keys[local] : 0ull;
+    val[i] = local < n ? in_vals[local] : 0u;
+  }
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * kRadixBits;
+    for (int t = tid; t < kSmallWarps * kRadix; t += kSmallThreads) (&sm.whist[0][0])[t] = 0;
+    __syncthreads();
+    uint32_t dig[kItems];
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t local = warp * (kItems * 32) + i * 32 + lane;
+      dig[i] = local < n ? (uint32_t)(key[i] >> shift) & (kRadix - 1) : kRadix;
+      const uint32_t peers = __match_any_sync(0xffffffffu, dig[i]);
+      uint32_t before = 0;
+      if (dig[i] < kRadix) before = sm.whist[warp][dig[i]];
+      rank[i] = before + __popc(peers & lt);
+      __syncwarp();
+      if (dig[i] < kRadix && (peers & lt) == 0) sm.whist[warp][dig[i]] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    if (tid < kRadix) {  // thread t owns digit t: per-warp offsets, tile offsets
+      uint32_t count = 0;
+#pragma unroll
+      for (int w = 0; w < kSmallWarps; ++w) {
+        const uint32_t c = sm.whist[w][tid];
+        sm.whist[w][tid] = count;
+        count += c;
+      }
+      uint32_t x = count;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) sm.wtot[warp] = x;
+      sm.lstart[tid] = x - count;  // within-warp part; warp prefix added below
+    }
+    __syncthreads();
+    if (tid < kRadix) {
+      uint32_t pre = 0;
+      for (int w = 0; w < warp; ++w) pre += sm.wtot[w];
+      sm.lstart[tid] += pre;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      if (dig[i] < kRadix) {
+        const uint32_t slot = sm.lstart[dig[i]] + sm.whist[warp][dig[i]] + rank[i];
+        sm.keys[slot] = key[i];
+        sm.vals[slot] = val[i];
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kItems; ++i) {
+      const uint32_t local = warp * (kItems * 32) + i * 32 + lane;
+      if (local < n) {
+        key[i] = sm.keys[local];
+        val[i] = sm.vals[local];
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < kItems; ++i) {
+    const uint32_t local = warp * (kItems * 32) + i * 32 + lane;
+    if (local < n) {
+      out_keys[local] = key[i];
+      out_vals[local] = val[i];
+    }
+  }
+}
+
 }  // namespace
 
 size_t sort_lookback_words(uint32_t n) {
@@ -224,6 +328,18 @@ cudaError_t launch_sort64(SortScratch sc, uint32_t n, int passes, int* out_buf, 
   *out_buf = 0;
   if (n <= 1 || passes <= 0) return cudaSuccess;
   if (passes > kPasses) passes = kPasses;
+  if (n <= kSmallTile) {  // one CTA, every pass in shared memory
+    const size_t smem = sizeof(SmallSortSmem);
+    cudaError_t e = cudaFuncSetAttribute(k_sort_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e) return e;
+    const int out = passes & 1;
+    k_sort_small<<<1, kSmallThreads, smem, s>>>(sc.keys[0], sc.vals[0], sc.keys[out], sc.vals[out],
+                                                n, passes);
+    note_launches(1);
+    *out_buf = out;
+    return cudaGetLastError();
+  }
   const uint32_t tiles = (n + kSortTile - 1) / kSortTile;
   cudaError_t e;
   if ((e = cudaMemsetAsync(sc.hist, 0, sizeof(uint32_t) * kPasses * kRadix, s))) return e;
