@@ -728,6 +728,8 @@ def main():
                                      "capture of the same workload at scale 0.15",
                      "peak_source": peak_src,
                      "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 8*(pairs in chunk)",
+                     "note": "the HBM-bound kernel of the step; the count pass (about as long, "
+                             "ALU-bound) is reported in roofline_count",
                      "write_ms_per_step": 1e3 * write_s / args.steps},
         "roofline_count": count_roofline(tests[0], d, count_ms, args.steps),
         "phases_ms_per_step": {
