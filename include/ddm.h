@@ -407,6 +407,14 @@ int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);
 int ddm_scan_counts_noalloc(const uint32_t *counts, uint32_t m, uint64_t *offsets,
                             void *stream);
 
+/* Test hook for the bounded device waits (failure detection without a
+ * fault): one warp polls a device word that nothing sets, with the same
+ * bounded wait as the sort's look-back, at most `polls` times (1..2^22, 64 ns
+ * apart), then records the timeout.  Returns DDM_ERR_TIMEOUT; the context
+ * stays usable.  DDM_ERR_ARG for polls out of range.  The paper has no
+ * counterpart. */
+int ddm_debug_wait_timeout(ddm_ctx *ctx, uint32_t polls, void *stream);
+
 /* Number of CUDA kernels this library has launched in the calling process
  * since it was loaded (all contexts).  Host-side counter, no GPU access. */
 uint64_t ddm_debug_launch_count(void);

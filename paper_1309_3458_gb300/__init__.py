@@ -70,6 +70,7 @@ SIGNATURES = {
     "ddm_set_replay_budget": (_i, [_vp, _u64]),
     "ddm_set_tuning": (_i, [_vp, _i, _u32, _u32]),
     "ddm_debug_launch_count": (_u64, []),
+    "ddm_debug_wait_timeout": (_i, [_vp, _u32, _vp]),
     "ddm_scan_counts_noalloc": (_i, [_vp, _u32, _vp, _vp]),
     "ddm_batch_match": (_i, [_vp, _i, _u32, _vp, _vp, _vp, _u32, _vp, _vp, _vp, _u32, _u32, _vp,
                              _u64, _vp, _pu64, _vp]),
@@ -359,6 +360,11 @@ def ddm_set_replay_budget(ctx: int, nbytes: int) -> None:
 
 def ddm_debug_set_alloc_limit(ctx: int, nbytes: int) -> None:
     _check(lib().ddm_debug_set_alloc_limit(ctx, nbytes), "ddm_debug_set_alloc_limit")
+
+
+def ddm_debug_wait_timeout(ctx: int, polls: int, stream=None) -> None:
+    """Make a bounded device wait run out (raises DDMError DDM_ERR_TIMEOUT)."""
+    _check(lib().ddm_debug_wait_timeout(ctx, polls, _stream(stream)), "ddm_debug_wait_timeout")
 
 
 def ddm_debug_launch_count() -> int:

@@ -57,6 +57,7 @@ struct ddm_ctx {
   DevBuf inst_s, inst_u, bglog2, bngroups, bgbase;
   // size classes of the tree order (d >= 2)
   DevBuf cls_hist, cls_off;
+  DevBuf probe;                 // word polled by ddm_debug_wait_timeout
   BatchView bv{};               // count 0 = single problem
   // tuning knobs (ddm_set_tuning)
   int str_shift = 0;            // added to the re-sort group exponents
@@ -577,7 +578,7 @@ int ddm_destroy(ddm_ctx* c) {
                     &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
                     &c->blk_pkt, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
                     &c->blk_list, &c->blk_counter, &c->inst_s, &c->inst_u, &c->bglog2,
-                    &c->bngroups, &c->bgbase, &c->cls_hist, &c->cls_off})
+                    &c->bngroups, &c->bgbase, &c->cls_hist, &c->cls_off, &c->probe})
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -599,6 +600,19 @@ int ddm_set_tuning(ddm_ctx* c, int str_shift, uint32_t ctas_per_sm, uint32_t rep
   c->ctas_per_sm = ctas_per_sm;
   c->replay_on = replay != 0;
   return DDM_OK;
+}
+
+int ddm_debug_wait_timeout(ddm_ctx* c, uint32_t polls, void* stream) {
+  if (!c || polls == 0 || polls > (1u << 22)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(ensure(c, c->probe, sizeof(uint32_t)));
+  DDM_CUDA(cudaMemsetAsync(c->probe.p, 0, sizeof(uint32_t), s));
+  DDM_TRY(reset_status(c, s));
+  DDM_CUDA(launch_debug_wait(static_cast<const uint32_t*>(c->probe.p), polls, c->st_dev, s));
+  DDM_TRY(sync_status(c, s));
+  return status_code(*c->st_host);
 }
 
 uint64_t ddm_debug_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

@@ -160,6 +160,9 @@ size_t sort_lookback_words(uint32_t n);
 // Stable LSD onesweep radix sort on the low 8*passes bits of 64-bit keys,
 // with a uint32 payload.  Input in keys[0]/vals[0]; *out_buf receives the
 // index (0 or 1) of the buffers holding the result.
+// Test hook: one warp polls `word` (which nothing sets) with the sort's
+// bounded wait, at most `limit` polls, and records kErrTimeout.
+cudaError_t launch_debug_wait(const uint32_t* word, uint32_t limit, Status* st, cudaStream_t s);
 cudaError_t launch_sort64(SortScratch sc, uint32_t n, int passes, int* out_buf, Status* st,
                           int sms, cudaStream_t s);
 

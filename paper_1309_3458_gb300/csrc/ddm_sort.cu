@@ -48,6 +48,30 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Bounded poll of a look-back word: returns it once any bit of `mask` is
+// set, or 0 with *timed_out after `limit` polls (64 ns apart), so that no
+// wait can outlive a predecessor that never publishes.
+__device__ __forceinline__ uint32_t poll_flag(const uint32_t* p, uint32_t mask, uint32_t limit,
+                                              bool* timed_out) {
+  for (uint32_t spins = 0;; ++spins) {
+    const uint32_t w = ld_relaxed(p);
+    if (w & mask) return w;
+    if (spins >= limit) {
+      *timed_out = true;
+      return 0u;
+    }
+    __nanosleep(64);
+  }
+}
+
+// Test hook for the bounded waits: poll a word nothing sets.
+__global__ void k_debug_wait(const uint32_t* __restrict__ word, uint32_t limit,
+                             Status* __restrict__ st) {
+  bool timed_out = false;
+  poll_flag(word, kFlagMask, limit, &timed_out);
+  if (timed_out && threadIdx.x == 0) atomicOr(&st->err, kErrTimeout);
+}
+
 // All eight digit histograms in one read of the keys.
 __global__ void __launch_bounds__(kThreads)
 k_histogram(const unsigned long long* __restrict__ keys, uint32_t n, uint32_t* __restrict__ hist) {
@@ -172,20 +196,17 @@ k_onesweep(const unsigned long long* __restrict__ in_keys, const uint32_t* __res
   // Decoupled look-back over earlier tiles for digit `tid`.
   uint32_t excl = 0;
   if (tile > 0) {
-    uint32_t p = tile - 1, spins = 0;
+    uint32_t p = tile - 1;
     for (;;) {
-      const uint32_t w = ld_relaxed(lookback + (size_t)p * kRadix + tid);
-      const uint32_t f = w & kFlagMask;
-      if (f == 0u) {
-        if (++spins > kSpinLimit) {
-          atomicOr(&st->err, kErrTimeout);
-          break;
-        }
-        __nanosleep(64);
-        continue;
+      bool timed_out = false;
+      const uint32_t w = poll_flag(lookback + (size_t)p * kRadix + tid, kFlagMask, kSpinLimit,
+                                   &timed_out);
+      if (timed_out) {
+        atomicOr(&st->err, kErrTimeout);
+        break;
       }
       excl += w & kValMask;
-      if (f == kFlagInc || p == 0) break;
+      if ((w & kFlagMask) == kFlagInc || p == 0) break;
       --p;
     }
     st_relaxed(my_slot, kFlagInc | (excl + count));
@@ -317,6 +338,12 @@ k_sort_small(const unsigned long long* __restrict__ in_keys, const uint32_t* __r
 }
 
 }  // namespace
+
+cudaError_t launch_debug_wait(const uint32_t* word, uint32_t limit, Status* st, cudaStream_t s) {
+  k_debug_wait<<<1, 32, 0, s>>>(word, limit, st);
+  note_launches(1);
+  return cudaGetLastError();
+}
 
 size_t sort_lookback_words(uint32_t n) {
   const size_t tiles = ((size_t)n + kSortTile - 1) / kSortTile;

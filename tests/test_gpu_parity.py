@@ -487,3 +487,16 @@ def test_size_and_dimension_limits(ctx):
     assert lib.ddm_count(ctx, 2, p, p, 4, p, p, 4, 8, ctypes.byref(k), s) == ddm.DDM_ERR_ARG  # flag
     # the context is still usable
     check_exact(ctx, W.uniform_fixed_length(300, 200, 2, 10.0, seed=1))
+
+
+def test_bounded_wait_times_out_and_context_survives(ctx):
+    """Failure detection without a GPU fault: a bounded device wait on a word
+    that nothing sets (the sort's look-back poll) gives up, the host reads
+    DDM_ERR_TIMEOUT, and the context keeps working."""
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.ddm_debug_wait_timeout(ctx, 1 << 14)
+    assert e.value.code == ddm.DDM_ERR_TIMEOUT
+    check_exact(ctx, W.uniform_fixed_length(5000, 4000, 2, 10.0, seed=3))
+    with pytest.raises(ddm.DDMError) as e:
+        ddm.ddm_debug_wait_timeout(ctx, 0)
+    assert e.value.code == ddm.DDM_ERR_ARG
