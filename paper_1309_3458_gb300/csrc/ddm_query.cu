@@ -7,8 +7,10 @@
 // (Alg. 1).  Queries are independent (Section IV, "Parallelizing ITM"), so
 // the GPU runs 32 of them per warp:
 //
-//   * the updates are sorted with the same spatial order as the tree (see
-//     ddm_layout.cu), so the 32 queries of a packet lie close together;
+//   * the updates are sorted by lower bound with the same sort-tile-recursive
+//     refinement as the tree (ddm_api.cu, order_set; the tree's size classes
+//     are not applied to queries), so the 32 queries of a packet lie close
+//     together;
 //   * the warp walks the flattened 32-ary tree depth-first with the packet's
 //     bounding box: one lane per child, one coalesced load of the children's
 //     per-dimension (minlower, maxupper), one ballot, a 32-bit mask of
@@ -17,13 +19,16 @@
 //     box meets the leaf's box are tested one after the other: every lane
 //     holds one subscription and applies the segment test of Alg. 1 in every
 //     dimension (the reduction of Section III-A), and a ballot yields that
-//     query's matches in the leaf.
+//     query's matches in the leaf; when many of them meet the leaf, the loops
+//     swap (lane = query, loop over the leaf's subscriptions).
 //
-// The count pass adds up matches per update; the write pass stores
-// (update, subscription) pairs from each update's output offset.  Both walk
-// the same leaves in the same order, so the write pass reproduces the
-// counted pairs exactly, in tree order.  Predicates are combined with
-// bitwise ANDs so the per-query test has no branches.
+// The count pass adds up matches per update and leaves replay records; the
+// write pass (k_replay) expands the records into (update, subscription)
+// pairs from each update's output offset, or, if the record arena ran out,
+// walks the tree again (k_packets with WRITE), visiting the same leaves in
+// the same order -- either way the pairs come out exactly as counted, in
+// tree order.  Predicates are combined with bitwise ANDs so the per-query
+// test has no branches.
 #include <cfloat>
 #include <type_traits>
 
