@@ -13,7 +13,11 @@
 // lower bound in the next dimension (k_rekey builds (group, key(lo_k))
 // keys).  Each group stays a contiguous range of the dimension-0 order, so
 // the top of the tree still follows the paper's lower-bound order, while the
-// small subtrees near the leaves become compact in every dimension.
+// small subtrees near the leaves become compact in every dimension.  For the
+// tree with d > 1 the subscriptions are first grouped by size class
+// (k_validate_class: class, then lower bound), and every class is refined
+// with groups sized for it (k_batch_groups / k_rekey_batch, the machinery of
+// batched sets with the classes as instances).
 #include "ddm_internal.cuh"
 
 namespace ddm {

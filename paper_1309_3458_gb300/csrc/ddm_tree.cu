@@ -14,7 +14,9 @@
 // The bounds are min/max reductions done with warp shuffles (32 children
 // per warp), level by level from the leaves up.  The element order comes
 // from ddm_layout.cu / ddm_sort.cu: dimension-0 (lower, upper, id), refined
-// inside aligned groups by the lower bound of the other dimensions.
+// inside aligned groups by the lower bound of the other dimensions (for
+// d > 1 within size classes of the extents); the bounds are computed from
+// the coordinates, so any order gives a correct tree.
 #include <cfloat>
 #include <cmath>
 
