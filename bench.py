@@ -68,6 +68,9 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="run only the serving run")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--no-sweep", action="store_true", help="skip the alpha x N sweep")
+    ap.add_argument("--phase", default="all", choices=["all", "build"],
+                    help="build: time ddm_build alone (sort + tree) on the workload's "
+                         "subscriptions, for profiling the build kernels")
     return ap.parse_args()
 
 
@@ -483,6 +486,35 @@ def sweep_section(reps: int = 3):
     return out
 
 
+def build_phase(args, ddm):
+    """ddm_build alone (validation, class keys, radix sort, re-sorts, tree
+    build) on the workload's subscription set."""
+    import torch
+    from paper_1309_3458_gb300 import workloads as W
+    a = W.make(args.config, args.scale)
+    lo, hi = torch.from_numpy(a[2]).cuda(), torch.from_numpy(a[3]).cuda()
+    ctx = ddm.ddm_create(torch.cuda.current_device())
+    stream = torch.cuda.current_stream()
+    try:
+        for _ in range(args.warmup):
+            ddm.ddm_build(ctx, lo, hi)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = ddm.ddm_debug_launch_count()
+        e0.record(stream)
+        for _ in range(args.steps):
+            ddm.ddm_build(ctx, lo, hi)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(1, args.steps)
+        launches = (ddm.ddm_debug_launch_count() - l0) // max(1, args.steps)
+    finally:
+        ddm.ddm_destroy(ctx)
+    n = lo.shape[1]
+    return {"phase": "build", "workload": args.config if args.scale == 1.0 else
+            f"{args.config}@{args.scale}", "n_sub": n, "d": lo.shape[0], "ms_per_build": ms,
+            "subscriptions_per_s": n / (ms / 1e3), "gpu_launches": int(launches)}
+
+
 def reference_arm(args, rank, world):
     if rank != 0:
         return
@@ -521,6 +553,9 @@ def main():
         return
     if args.serving_only:
         print(json.dumps({"serving": serving_section(args.serving_seconds)}), flush=True)
+        return
+    if args.phase == "build":
+        print(json.dumps(build_phase(args, ddm)), flush=True)
         return
     if world > 1:
         tdist.init_process_group("nccl")
