@@ -163,7 +163,7 @@ class Clocks:
                 "samples": len(mhz)}
 
 
-def cpu_oracle_sample(arrays, budget_s):
+def cpu_oracle_sample(arrays, budget_s, one_core: bool = False):
     """Oracle ITM (all host cores) on a bounded sample of the workload: one
     interval tree build over all subscriptions plus a random sample of the
     updates; pairs/s extrapolated to the whole update set (one build, all
@@ -189,12 +189,46 @@ def cpu_oracle_sample(arrays, budget_s):
     wall = time.perf_counter() - t0
     t_build, t_q = tm
     t_all = t_build + t_q * m / q
-    return {"value": K * m / q / t_all, "unit": "pairs/s", "cores": threads, "kind": "oracle",
-            "sample": (f"interval tree (AVL) build over all {slo.shape[1]} subscriptions "
-                       f"({t_build:.2f} s) + {q} of {m} updates queried with OpenMP on "
-                       f"{threads} threads ({t_q:.2f} s, {K} pairs); rate extrapolated to all "
-                       f"updates"),
-            "queries_per_s": m / t_all, "seconds": wall}
+    out = {"value": K * m / q / t_all, "unit": "pairs/s", "cores": threads, "kind": "oracle",
+           "sample": (f"interval tree (AVL) build over all {slo.shape[1]} subscriptions "
+                      f"({t_build:.2f} s) + {q} of {m} updates queried with OpenMP on "
+                      f"{threads} threads ({t_q:.2f} s, {K} pairs); rate extrapolated to all "
+                      f"updates"),
+           "queries_per_s": m / t_all, "seconds": wall}
+    if one_core:
+        # the sequential ITM (one thread), on a quarter of the sample
+        s1 = np.sort(rng.choice(m, max(64, q // 4), replace=False))
+        tm = []
+        K1, _, _ = oracle.itm_count(*sub(s1), slo, shi, threads=1, timings=tm)
+        t1 = tm[0] + tm[1] * m / len(s1)
+        out["one_core"] = {"value": K1 * m / len(s1) / t1, "unit": "pairs/s",
+                           "sample": f"{len(s1)} of {m} updates on one thread, same extrapolation",
+                           "queries_per_s": m / t1}
+    return out
+
+
+def cpu_small_configs():
+    """The oracle on the N = 1e4, d = 1 workload: brute force (Alg. 2) on one
+    thread and the interval tree (Algs. 4-5, build included) on one thread
+    and on all host cores."""
+    import numpy as np
+
+    import oracle
+    from paper_1309_3458_gb300 import workloads as W
+    a = W.make("uniform_d1_N1e4_a1")
+    threads = len(os.sched_getaffinity(0))
+    out = {"workload": "uniform_d1_N1e4_a1"}
+    t0 = time.perf_counter()
+    K = oracle.bf(*a, pairs=False)[0]
+    out["bf_1core_s"] = time.perf_counter() - t0
+    for name, th in (("itm_1core_s", 1), ("itm_all_cores_s", threads)):
+        t0 = time.perf_counter()
+        Ki, _, _ = oracle.itm_count(*a, threads=th)
+        out[name] = time.perf_counter() - t0
+        assert Ki == K
+    out["K"] = int(K)
+    out["cores"] = threads
+    return out
 
 
 def batched_section(reps: int = 3):
@@ -730,8 +764,9 @@ def main():
 
     cpu = None
     if not args.no_cpu and world == 1:
-        cpu = cpu_oracle_sample(arrays, args.cpu_seconds)
+        cpu = cpu_oracle_sample(arrays, args.cpu_seconds, one_core=True)
         cpu.pop("seconds", None)
+        cpu["small_configs"] = cpu_small_configs()
 
     clocks = clk.summary()
     line = {
