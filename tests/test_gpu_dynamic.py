@@ -14,23 +14,23 @@ from tests.helpers import keys, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def fresh_pairs(ctx, U):
+def fresh_pairs(ctx, U, flags=0):
     import torch
-    K = ddm.ddm_count(ctx, *U)
+    K = ddm.ddm_count(ctx, *U, flags=flags)
     buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
-    ddm.ddm_match(ctx, *U, buf)
+    ddm.ddm_match(ctx, *U, buf, flags=flags)
     return buf[:K].cpu().numpy().view(np.uint32).copy()
 
 
-@pytest.mark.parametrize("d", [1, 2, 3])
-def test_moved_rows_and_columns(d):
+@pytest.mark.parametrize("d,flags", [(1, 0), (2, 0), (3, 0), (2, 1)])
+def test_moved_rows_and_columns(d, flags):
     import torch
     import __graft_entry__
     __graft_entry__.build()
     rng = np.random.default_rng(d)
     a = W.uniform_fixed_length(6000, 5000, d, 30.0, seed=d)
     U = to_dev(a)
-    dm = DynamicMatching(*U, rebuild_every=3)
+    dm = DynamicMatching(*U, flags=flags, rebuild_every=3)
     ctx = ddm.ddm_create(0)
     buf = torch.empty((1 << 22, 2), dtype=torch.int32, device="cuda")
     l = float(a[1][0, 0] - a[0][0, 0])
@@ -51,7 +51,7 @@ def test_moved_rows_and_columns(d):
             else:
                 K = dm.move_subscriptions(ids, lo, hi, buf)
             got = buf[:K].cpu().numpy().view(np.uint32)
-            full = fresh_pairs(ctx, dm.sets())
+            full = fresh_pairs(ctx, dm.sets(), flags)
             col = 0 if kind == 0 else 1
             want = full[np.isin(full[:, col], ids_np.astype(np.uint32))]
             assert K == len(want)
@@ -65,7 +65,7 @@ def test_moved_rows_and_columns(d):
         K = dm.match_all(buf)
         got = buf[:K].cpu().numpy().view(np.uint32)
         host = [x.cpu().numpy() for x in dm.sets()]
-        Ko, ou, os_ = oracle.itm_pairs(*host)
+        Ko, ou, os_ = oracle.itm_pairs(*host, flags=flags)
         assert K == Ko
         assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(ou, os_)))
     finally:

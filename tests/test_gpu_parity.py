@@ -264,15 +264,16 @@ def test_staged_chunks_reproduce_full_output(ctx):
     assert np.array_equal(sl[:, 1], ps[off[1234]:off[4321]])
 
 
-def test_ordered_chunks_cover_the_same_pairs(ctx):
+@pytest.mark.parametrize("flags", [0, 1])
+def test_ordered_chunks_cover_the_same_pairs(ctx, flags):
     import torch
     arrays = W.clustered_lognormal(40000, 30000, d=3, alpha=100.0, seed=12)
-    K, pu, ps = gpu_match(ctx, arrays)
+    K, pu, ps = gpu_match(ctx, arrays, flags)
     U = to_dev(arrays)
     ddm.ddm_build(ctx, U[2], U[3])
     m = 30000
     off = torch.empty(m + 1, dtype=torch.int64, device="cuda")
-    assert ddm.ddm_plan(ctx, U[0], U[1], offsets=off) == K
+    assert ddm.ddm_plan(ctx, U[0], U[1], flags=flags, offsets=off) == K
     order = torch.empty(m, dtype=torch.int32, device="cuda")
     ooff = torch.empty(m + 1, dtype=torch.int64, device="cuda")
     ddm.ddm_plan_order(ctx, order, ooff)
