@@ -25,8 +25,9 @@ from __future__ import annotations
 import math
 import threading
 import time
-from dataclasses import dataclass, field
-from typing import Any, Dict, List, Optional
+from collections import deque
+from dataclasses import dataclass
+from typing import Any, Deque, Dict, List, Optional
 
 import numpy as np
 
@@ -381,7 +382,7 @@ class Server:
                 break
             if (batch or self.reserved) and self.reserved + r.est_bytes > self.budget:
                 break
-            self.waiting.pop(0)
+            self.waiting.popleft()
             self.reserved += r.est_bytes
             r.admitted = time.perf_counter() - self.t0
             batch.append(r)
@@ -390,16 +391,15 @@ class Server:
         return batch
 
     def _serve(self, schedule, timeout_s):
-        pending = list(schedule)
-        pending.reverse()
-        self.waiting: List[Request] = []
+        pending = deque(sorted(schedule, key=lambda r: r.arrival))
+        self.waiting: Deque[Request] = deque()
         finished: List[Request] = []
         while len(finished) < len(schedule):
             now = time.perf_counter() - self.t0
             if now > timeout_s:
                 raise TimeoutError("serving run did not finish")
-            while pending and pending[-1].arrival <= now:
-                self.waiting.append(pending.pop())
+            while pending and pending[0].arrival <= now:
+                self.waiting.append(pending.popleft())
             for slot in self.slots:  # completions
                 if slot["batch"] is not None and slot["event"].query():
                     finished.extend(slot["batch"])

@@ -20,7 +20,7 @@ import pytest
 import oracle
 import paper_1309_3458_gb300 as ddm
 from paper_1309_3458_gb300 import workloads as W
-from tests.helpers import gpu_match, gpu_offsets, keys, to_dev
+from tests.helpers import gpu_match, keys, to_dev
 
 pytestmark = pytest.mark.gpu
 
