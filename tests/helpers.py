@@ -22,16 +22,6 @@ def gpu_match(ctx, arrays, flags=0, dev=None):
     return K, p[:, 0].copy(), p[:, 1].copy()
 
 
-def gpu_offsets(ctx, arrays, flags=0, dev=None):
-    """Build + plan; returns (K, offsets[m+1]) as numpy."""
-    import torch
-    U = dev if dev is not None else to_dev(arrays)
-    ddm.ddm_build(ctx, U[2], U[3])
-    off = torch.empty(U[0].shape[1] + 1, dtype=torch.int64, device="cuda")
-    K = ddm.ddm_plan(ctx, U[0], U[1], flags=flags, offsets=off)
-    return K, off.cpu().numpy().astype(np.uint64)
-
-
 def keys(pu, ps):
     return (pu.astype(np.uint64) << np.uint64(32)) | ps.astype(np.uint64)
 
