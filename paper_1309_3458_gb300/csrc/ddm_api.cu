@@ -58,6 +58,7 @@ struct ddm_ctx {
   // size classes of the tree order (d >= 2)
   DevBuf cls_hist, cls_off;
   DevBuf probe;                 // word polled by ddm_debug_wait_timeout
+  DevBuf aos;                   // interleaved coordinates of the set being ordered
   BatchView bv{};               // count 0 = single problem
   // tuning knobs (ddm_set_tuning)
   int str_shift = 0;            // added to the re-sort group exponents
@@ -116,6 +117,13 @@ int ensure(ddm_ctx* c, DevBuf& b, size_t bytes) {
   b.cap = want;
   c->allocated += want;
   return DDM_OK;
+}
+
+// Interleaved copy of a set's coordinates for the gathers by id; NULL (the
+// gathers then read the caller's rows) if it cannot be allocated.
+float2* aos_buffer(ddm_ctx* c, int d, uint32_t cnt) {
+  if (cnt == 0 || ensure(c, c->aos, sizeof(float2) * (size_t)d * cnt) != DDM_OK) return nullptr;
+  return static_cast<float2*>(c->aos.p);
 }
 
 void release(DevBuf& b) {
@@ -208,7 +216,7 @@ struct BatchSet {
 };
 
 int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
-                    const BatchSet& bs, int* cur, cudaStream_t s) {
+                    const BatchSet& bs, float2* aos, int* cur, cudaStream_t s) {
   *cur = 0;
   DDM_TRY(ensure_sort(c, cnt));
   DDM_TRY(ensure(c, c->bglog2, sizeof(int) * (bs.count ? bs.count : 1)));
@@ -218,7 +226,7 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
   DDM_CUDA(launch_fill_inst(bs.off, bs.count, bs.inst, s));
   DDM_CUDA(launch_validate_batch(d, lo, hi, cnt, bs.inst,
                                  static_cast<unsigned long long*>(c->keys[0].p),
-                                 static_cast<uint32_t*>(c->vals[0].p), c->st_dev, c->sms, s));
+                                 static_cast<uint32_t*>(c->vals[0].p), aos, c->st_dev, c->sms, s));
   DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(bs.count ? bs.count - 1 : 0), cur, s));
   for (int k = 1; k < d; ++k) {
     auto* gl = static_cast<int*>(c->bglog2.p);
@@ -237,8 +245,8 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
 // Tree order for d >= 2: sort by (size class, lower bound), then refine
 // each class by the sort-tile-recursive re-sorts of its own size (the
 // per-instance machinery of batched sets, with the classes as instances).
-int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt, int* cur,
-                      cudaStream_t s) {
+int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
+                      float2* aos, int* cur, cudaStream_t s) {
   constexpr uint32_t kClasses = 256;
   *cur = 0;
   DDM_TRY(ensure_sort(c, cnt));
@@ -255,7 +263,8 @@ int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint3
   auto* sums = static_cast<unsigned long long*>(c->sums.p);
   DDM_CUDA(cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kClasses, s));
   DDM_CUDA(launch_validate_class(d, lo, hi, cnt, static_cast<unsigned long long*>(c->keys[0].p),
-                                 static_cast<uint32_t*>(c->vals[0].p), hist, c->st_dev, c->sms, s));
+                                 static_cast<uint32_t*>(c->vals[0].p), hist, aos, c->st_dev,
+                                 c->sms, s));
   DDM_TRY(sort_pass(c, cnt, 8, cur, s));
   DDM_CUDA(launch_scan(hist, kClasses, off, sums, nullptr, s));
   DDM_CUDA(launch_fill_inst(off, kClasses, inst, s));
@@ -274,12 +283,12 @@ int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint3
 }
 
 int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt, bool tree,
-              int* cur, cudaStream_t s) {
+              float2* aos, int* cur, cudaStream_t s) {
   *cur = 0;
   DDM_TRY(ensure_sort(c, cnt));
   DDM_CUDA(launch_validate(d, lo, hi, cnt, static_cast<unsigned long long*>(c->keys[0].p),
-                           static_cast<uint32_t*>(c->vals[0].p), tree ? 1 : 2, c->st_dev, c->sms,
-                           s));
+                           static_cast<uint32_t*>(c->vals[0].p), tree ? 1 : 2, aos, c->st_dev,
+                           c->sms, s));
   DDM_TRY(sort_pass(c, cnt, tree ? 8 : 4, cur, s));
   int glog2[DDM_MAX_DIMS];
   str_groups(cnt, d, glog2, c->str_shift);
@@ -316,16 +325,17 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
   DDM_TRY(ensure(c, c->sid, sizeof(uint32_t) * n));
   DDM_TRY(ensure(c, c->nodes, sizeof(float2) * (size_t)d * t.total));
   int cur = 0;
+  float2* aos = aos_buffer(c, d, n);
   if (bs)
-    DDM_TRY(order_set_batch(c, d, slo, shi, n, *bs, &cur, s));
+    DDM_TRY(order_set_batch(c, d, slo, shi, n, *bs, aos, &cur, s));
   else if (d >= 2)
-    DDM_TRY(order_set_classes(c, d, slo, shi, n, &cur, s));
+    DDM_TRY(order_set_classes(c, d, slo, shi, n, aos, &cur, s));
   else
-    DDM_TRY(order_set(c, d, slo, shi, n, true, &cur, s));
+    DDM_TRY(order_set(c, d, slo, shi, n, true, aos, &cur, s));
   t.e = static_cast<const float2*>(c->e.p);
   t.sid = static_cast<const uint32_t*>(c->sid.p);
   t.nodes = static_cast<const float2*>(c->nodes.p);
-  DDM_CUDA(launch_build(t, static_cast<const uint32_t*>(c->vals[cur].p), slo, shi,
+  DDM_CUDA(launch_build(t, static_cast<const uint32_t*>(c->vals[cur].p), slo, shi, aos,
                         static_cast<float2*>(c->e.p), static_cast<uint32_t*>(c->sid.p),
                         static_cast<float2*>(c->nodes.p), s));
   c->tree = t;
@@ -419,11 +429,12 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   }
   if (m > 0) {
     int cur = 0;
+    float2* aos = aos_buffer(c, d, m);
     if (bs)
-      DDM_TRY(order_set_batch(c, d, ulo, uhi, m, *bs, &cur, s));
+      DDM_TRY(order_set_batch(c, d, ulo, uhi, m, *bs, aos, &cur, s));
     else
-      DDM_TRY(order_set(c, d, ulo, uhi, m, false, &cur, s));
-    DDM_CUDA(launch_gather(d, static_cast<const uint32_t*>(c->vals[cur].p), ulo, uhi, m,
+      DDM_TRY(order_set(c, d, ulo, uhi, m, false, aos, &cur, s));
+    DDM_CUDA(launch_gather(d, static_cast<const uint32_t*>(c->vals[cur].p), ulo, uhi, aos, m,
                            static_cast<float2*>(c->qe.p), static_cast<uint32_t*>(c->qid.p), c->sms,
                            s));
     if (c->tree.n > 0) {
@@ -578,7 +589,7 @@ int ddm_destroy(ddm_ctx* c) {
                     &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
                     &c->blk_pkt, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
                     &c->blk_list, &c->blk_counter, &c->inst_s, &c->inst_u, &c->bglog2,
-                    &c->bngroups, &c->bgbase, &c->cls_hist, &c->cls_off, &c->probe})
+                    &c->bngroups, &c->bgbase, &c->cls_hist, &c->cls_off, &c->probe, &c->aos})
     release(*b);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
@@ -934,11 +945,12 @@ int ddm_refit(ddm_ctx* c, const float* sub_lo, const float* sub_hi, void* stream
   DDM_TRY(reset_status(c, s));
   c->planned = false;
   if (c->tree.n > 0) {
-    DDM_CUDA(launch_validate(c->tree.d, sub_lo, sub_hi, c->tree.n, nullptr, nullptr, 0, c->st_dev,
-                             c->sms, s));
+    float2* aos = aos_buffer(c, c->tree.d, c->tree.n);
+    DDM_CUDA(launch_validate(c->tree.d, sub_lo, sub_hi, c->tree.n, nullptr, nullptr, 0, aos,
+                             c->st_dev, c->sms, s));
     // Same order, new coordinates: gather through the tree's own id column and
     // recompute every node's per-dimension (minlower, maxupper).
-    DDM_CUDA(launch_build(c->tree, c->tree.sid, sub_lo, sub_hi, static_cast<float2*>(c->e.p),
+    DDM_CUDA(launch_build(c->tree, c->tree.sid, sub_lo, sub_hi, aos, static_cast<float2*>(c->e.p),
                           static_cast<uint32_t*>(c->sid.p), static_cast<float2*>(c->nodes.p), s));
   }
   DDM_TRY(sync_status(c, s));

@@ -116,9 +116,13 @@ void note_launches(unsigned count);
 // Validate a set (lo <= hi, no NaN in every dimension) and, when keys is
 // not null, emit the sort key with the identity payload: key_mode 1 gives
 // (key(lo0) << 32 | key(hi0)) (tree order), key_mode 2 gives key(lo0).
+// aos (optional, cnt * d float2): an interleaved copy of the coordinates,
+// aos[i*d + k] = (lo_k, hi_k) of extent i, written while validating, so that
+// the gathers by id read one contiguous record per extent instead of 2d
+// scattered words.
 cudaError_t launch_validate(int d, const float* lo, const float* hi, uint32_t cnt,
-                            unsigned long long* keys, uint32_t* vals, int key_mode, Status* st,
-                            int sms, cudaStream_t s);
+                            unsigned long long* keys, uint32_t* vals, int key_mode, float2* aos,
+                            Status* st, int sms, cudaStream_t s);
 // keys[i] = (i >> glog2) << 32 | key(lo_k[vals[i]]): re-sort inside groups.
 cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, int glog2,
                          unsigned long long* keys, int sms, cudaStream_t s);
@@ -127,13 +131,13 @@ cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, 
 // caller) receives the number of extents of each size class.
 cudaError_t launch_validate_class(int d, const float* lo, const float* hi, uint32_t cnt,
                                   unsigned long long* keys, uint32_t* vals, uint32_t* hist,
-                                  Status* st, int sms, cudaStream_t s);
+                                  float2* aos, Status* st, int sms, cudaStream_t s);
 cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t* inst,
                              cudaStream_t s);
 // Batched validation + keys: keys[i] = inst[i] << 32 | key(lo0[i]).
 cudaError_t launch_validate_batch(int d, const float* lo, const float* hi, uint32_t cnt,
                                   const uint32_t* inst, unsigned long long* keys, uint32_t* vals,
-                                  Status* st, int sms, cudaStream_t s);
+                                  float2* aos, Status* st, int sms, cudaStream_t s);
 // Per instance and dimension k >= 1: group exponent (0 = groups of 1) and
 // group count, for the batched re-sorts.  glog2/ngroups: [count] each.
 cudaError_t launch_batch_groups(const unsigned long long* off, uint32_t count, int d, int k,
@@ -145,7 +149,8 @@ cudaError_t launch_rekey_batch(const uint32_t* vals, const float* lo_k, uint32_t
                                unsigned long long* keys, int sms, cudaStream_t s);
 // qe[k][i] = (lo_k, hi_k)[vals[i]], qid[i] = vals[i].
 cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const float* hi,
-                          uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s);
+                          const float2* aos, uint32_t cnt, float2* qe, uint32_t* qid, int sms,
+                          cudaStream_t s);
 
 // ---- ddm_sort.cu ----------------------------------------------------------
 struct SortScratch {
@@ -173,8 +178,8 @@ void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* tota
 // `shift` is added to every exponent (tuning knob, 0 = the STR sizes).
 void str_groups(uint32_t n, int d, int* glog2, int shift = 0);
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
-                         const float* hi, float2* e, uint32_t* sid, float2* nodes,
-                         cudaStream_t s);
+                         const float* hi, const float2* aos, float2* e, uint32_t* sid,
+                         float2* nodes, cudaStream_t s);
 cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s);
 
 // ---- ddm_query.cu ---------------------------------------------------------

@@ -28,7 +28,7 @@ constexpr int kThreads = 256;
 __global__ void __launch_bounds__(kThreads)
 k_validate(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
            unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals, int key_mode,
-           Status* __restrict__ st) {
+           float2* __restrict__ aos, Status* __restrict__ st) {
   bool bad = false;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
@@ -37,6 +37,7 @@ k_validate(int d, const float* __restrict__ lo, const float* __restrict__ hi, ui
       const float a = __ldg(lo + (size_t)k * cnt + i);
       const float b = __ldg(hi + (size_t)k * cnt + i);
       bad |= !(a <= b);  // false for NaN as well as for lo > hi
+      if (aos) aos[(size_t)i * d + k] = make_float2(a, b);
     }
     if (keys) {
       const float a = __ldg(lo + i), b = __ldg(hi + i);
@@ -58,15 +59,16 @@ k_rekey(const uint32_t* __restrict__ vals, const float* __restrict__ lo_k, uint3
 
 __global__ void __launch_bounds__(kThreads)
 k_gather(int d, const uint32_t* __restrict__ vals, const float* __restrict__ lo,
-         const float* __restrict__ hi, uint32_t cnt, float2* __restrict__ qe,
-         uint32_t* __restrict__ qid) {
+         const float* __restrict__ hi, const float2* __restrict__ aos, uint32_t cnt,
+         float2* __restrict__ qe, uint32_t* __restrict__ qid) {
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
     const uint32_t id = vals[i];
     qid[i] = id;
     for (int k = 0; k < d; ++k)
-      qe[(size_t)k * cnt + i] = make_float2(__ldg(lo + (size_t)k * cnt + id),
-                                            __ldg(hi + (size_t)k * cnt + id));
+      qe[(size_t)k * cnt + i] = aos ? aos[(size_t)id * d + k]
+                                    : make_float2(__ldg(lo + (size_t)k * cnt + id),
+                                                  __ldg(hi + (size_t)k * cnt + id));
   }
 }
 
@@ -80,7 +82,7 @@ k_gather(int d, const uint32_t* __restrict__ vals, const float* __restrict__ lo,
 __global__ void __launch_bounds__(kThreads)
 k_validate_class(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
                  unsigned long long* __restrict__ keys, uint32_t* __restrict__ vals,
-                 uint32_t* __restrict__ hist, Status* __restrict__ st) {
+                 uint32_t* __restrict__ hist, float2* __restrict__ aos, Status* __restrict__ st) {
   __shared__ uint32_t s_h[256];
   for (int i = threadIdx.x; i < 256; i += blockDim.x) s_h[i] = 0u;
   __syncthreads();
@@ -93,6 +95,7 @@ k_validate_class(int d, const float* __restrict__ lo, const float* __restrict__ 
       const float b = __ldg(hi + (size_t)k * cnt + i);
       bad |= !(a <= b);
       side = fmaxf(side, b - a);
+      if (aos) aos[(size_t)i * d + k] = make_float2(a, b);
     }
     const uint32_t cls = (__float_as_uint(side) >> 23) & 0xffu;
     keys[i] = ((unsigned long long)cls << 56) |
@@ -116,7 +119,7 @@ __global__ void k_fill_inst(const unsigned long long* __restrict__ off, uint32_t
 __global__ void __launch_bounds__(kThreads)
 k_validate_batch(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
                  const uint32_t* __restrict__ inst, unsigned long long* __restrict__ keys,
-                 uint32_t* __restrict__ vals, Status* __restrict__ st) {
+                 uint32_t* __restrict__ vals, float2* __restrict__ aos, Status* __restrict__ st) {
   bool bad = false;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
@@ -124,6 +127,7 @@ k_validate_batch(int d, const float* __restrict__ lo, const float* __restrict__ 
       const float a = __ldg(lo + (size_t)k * cnt + i);
       const float b = __ldg(hi + (size_t)k * cnt + i);
       bad |= !(a <= b);
+      if (aos) aos[(size_t)i * d + k] = make_float2(a, b);
     }
     keys[i] = ((unsigned long long)inst[i] << 32) | float_key(__ldg(lo + i));
     vals[i] = i;
@@ -178,18 +182,20 @@ cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, 
 }
 
 cudaError_t launch_gather(int d, const uint32_t* vals, const float* lo, const float* hi,
-                          uint32_t cnt, float2* qe, uint32_t* qid, int sms, cudaStream_t s) {
+                          const float2* aos, uint32_t cnt, float2* qe, uint32_t* qid, int sms,
+                          cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
-  k_gather<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, vals, lo, hi, cnt, qe, qid);
+  k_gather<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, vals, lo, hi, aos, cnt, qe, qid);
   note_launches(1);
   return cudaGetLastError();
 }
 
 cudaError_t launch_validate_class(int d, const float* lo, const float* hi, uint32_t cnt,
                                   unsigned long long* keys, uint32_t* vals, uint32_t* hist,
-                                  Status* st, int sms, cudaStream_t s) {
+                                  float2* aos, Status* st, int sms, cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
-  k_validate_class<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, keys, vals, hist, st);
+  k_validate_class<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, keys, vals, hist, aos,
+                                                           st);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -204,9 +210,10 @@ cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint
 
 cudaError_t launch_validate_batch(int d, const float* lo, const float* hi, uint32_t cnt,
                                   const uint32_t* inst, unsigned long long* keys, uint32_t* vals,
-                                  Status* st, int sms, cudaStream_t s) {
+                                  float2* aos, Status* st, int sms, cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
-  k_validate_batch<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, inst, keys, vals, st);
+  k_validate_batch<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, inst, keys, vals, aos,
+                                                           st);
   note_launches(1);
   return cudaGetLastError();
 }
@@ -232,10 +239,11 @@ cudaError_t launch_rekey_batch(const uint32_t* vals, const float* lo_k, uint32_t
 }
 
 cudaError_t launch_validate(int d, const float* lo, const float* hi, uint32_t cnt,
-                            unsigned long long* keys, uint32_t* vals, int key_mode, Status* st,
-                            int sms, cudaStream_t s) {
+                            unsigned long long* keys, uint32_t* vals, int key_mode, float2* aos,
+                            Status* st, int sms, cudaStream_t s) {
   if (cnt == 0) return cudaSuccess;
-  k_validate<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, keys, vals, key_mode, st);
+  k_validate<<<grid_for(cnt, sms), kThreads, 0, s>>>(d, lo, hi, cnt, keys, vals, key_mode, aos,
+                                                     st);
   note_launches(1);
   return cudaGetLastError();
 }

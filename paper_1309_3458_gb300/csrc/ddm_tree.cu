@@ -42,8 +42,8 @@ __device__ __forceinline__ float warp_min(float v) {
 // CTA's 32 level-1 nodes form level-2 node blockIdx.x.
 __global__ void __launch_bounds__(1024)
 k_gather_build(TreeView t, const uint32_t* __restrict__ sorted_ids, const float* __restrict__ lo,
-               const float* __restrict__ hi, float2* __restrict__ e, uint32_t* __restrict__ sid,
-               float2* __restrict__ nodes) {
+               const float* __restrict__ hi, const float2* __restrict__ aos,
+               float2* __restrict__ e, uint32_t* __restrict__ sid, float2* __restrict__ nodes) {
   __shared__ float s_min[DDM_MAX_DIMS][32], s_max[DDM_MAX_DIMS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t n = t.n;
@@ -59,8 +59,14 @@ k_gather_build(TreeView t, const uint32_t* __restrict__ sorted_ids, const float*
   for (int k = 0; k < t.d; ++k) {
     float a = FLT_MAX, b = -FLT_MAX;
     if (valid) {
-      a = lo[(size_t)k * n + id];
-      b = hi[(size_t)k * n + id];
+      if (aos) {
+        const float2 v = aos[(size_t)id * t.d + k];
+        a = v.x;
+        b = v.y;
+      } else {
+        a = lo[(size_t)k * n + id];
+        b = hi[(size_t)k * n + id];
+      }
       e[(size_t)k * n + i] = make_float2(a, b);
     }
     const float mn = warp_min(valid ? a : INFINITY);
@@ -143,11 +149,11 @@ void str_groups(uint32_t n, int d, int* glog2, int shift) {
 }
 
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
-                         const float* hi, float2* e, uint32_t* sid, float2* nodes,
-                         cudaStream_t s) {
+                         const float* hi, const float2* aos, float2* e, uint32_t* sid,
+                         float2* nodes, cudaStream_t s) {
   if (t.n == 0) return cudaSuccess;
   const uint32_t blocks = (t.n + 1023) / 1024;
-  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, e, sid, nodes);
+  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, aos, e, sid, nodes);
   if (t.L >= 3) k_build_upper<<<1, 1024, 0, s>>>(t, nodes);
   note_launches(t.L >= 3 ? 2u : 1u);
   return cudaGetLastError();
