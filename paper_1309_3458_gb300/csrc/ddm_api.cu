@@ -223,7 +223,7 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
   DDM_TRY(ensure(c, c->bngroups, sizeof(uint32_t) * (bs.count ? bs.count : 1)));
   DDM_TRY(ensure(c, c->bgbase, sizeof(unsigned long long) * ((size_t)bs.count + 1)));
   DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * ((size_t)cnt / kScanTile + (size_t)bs.count / kScanTile + 2)));
-  DDM_CUDA(launch_fill_inst(bs.off, bs.count, bs.inst, s));
+  DDM_CUDA(launch_fill_inst(bs.off, bs.count, cnt, bs.inst, c->sms, s));
   DDM_CUDA(launch_validate_batch(d, lo, hi, cnt, bs.inst,
                                  static_cast<unsigned long long*>(c->keys[0].p),
                                  static_cast<uint32_t*>(c->vals[0].p), aos, c->st_dev, c->sms, s));
@@ -267,7 +267,7 @@ int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint3
                                  c->sms, s));
   DDM_TRY(sort_pass(c, cnt, 8, cur, s));
   DDM_CUDA(launch_scan(hist, kClasses, off, sums, nullptr, s));
-  DDM_CUDA(launch_fill_inst(off, kClasses, inst, s));
+  DDM_CUDA(launch_fill_inst(off, kClasses, cnt, inst, c->sms, s));
   for (int k = 1; k < d; ++k) {
     auto* gl = static_cast<int*>(c->bglog2.p);
     auto* ng = static_cast<uint32_t*>(c->bngroups.p);

@@ -132,8 +132,9 @@ cudaError_t launch_rekey(const uint32_t* vals, const float* lo_k, uint32_t cnt, 
 cudaError_t launch_validate_class(int d, const float* lo, const float* hi, uint32_t cnt,
                                   unsigned long long* keys, uint32_t* vals, uint32_t* hist,
                                   float2* aos, Status* st, int sms, cudaStream_t s);
-cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t* inst,
-                             cudaStream_t s);
+// inst[i] = the b with off[b] <= i < off[b+1], for 0 <= i < total.
+cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t total,
+                             uint32_t* inst, int sms, cudaStream_t s);
 // Batched validation + keys: keys[i] = inst[i] << 32 | key(lo0[i]).
 cudaError_t launch_validate_batch(int d, const float* lo, const float* hi, uint32_t cnt,
                                   const uint32_t* inst, unsigned long long* keys, uint32_t* vals,

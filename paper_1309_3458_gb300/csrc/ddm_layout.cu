@@ -110,10 +110,21 @@ k_validate_class(int d, const float* __restrict__ lo, const float* __restrict__ 
     if (s_h[i]) atomicAdd(&hist[i], s_h[i]);
 }
 
-// Batched sets: one CTA per instance marks its positions.
-__global__ void k_fill_inst(const unsigned long long* __restrict__ off, uint32_t* __restrict__ inst) {
-  const unsigned long long b = off[blockIdx.x], e = off[blockIdx.x + 1];
-  for (unsigned long long i = b + threadIdx.x; i < e; i += blockDim.x) inst[i] = blockIdx.x;
+// Instance (batched set, or size class) of every position: the b with
+// off[b] <= i < off[b+1], by binary search over the offsets, so that one
+// very large instance is filled by the whole grid.
+__global__ void __launch_bounds__(kThreads)
+k_fill_inst(const unsigned long long* __restrict__ off, uint32_t count, uint32_t total,
+            uint32_t* __restrict__ inst) {
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += stride) {
+    uint32_t lo = 0, hi = count;  // off[lo] <= i < off[hi]
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (off[mid] <= i) lo = mid; else hi = mid;
+    }
+    inst[i] = lo;
+  }
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -200,10 +211,10 @@ cudaError_t launch_validate_class(int d, const float* lo, const float* hi, uint3
   return cudaGetLastError();
 }
 
-cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t* inst,
-                             cudaStream_t s) {
-  if (count == 0) return cudaSuccess;
-  k_fill_inst<<<count, 256, 0, s>>>(off, inst);
+cudaError_t launch_fill_inst(const unsigned long long* off, uint32_t count, uint32_t total,
+                             uint32_t* inst, int sms, cudaStream_t s) {
+  if (count == 0 || total == 0) return cudaSuccess;
+  k_fill_inst<<<grid_for(total, sms), kThreads, 0, s>>>(off, count, total, inst);
   note_launches(1);
   return cudaGetLastError();
 }
