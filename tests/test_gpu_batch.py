@@ -138,3 +138,31 @@ def test_batch_errors(ctx):
     rc = ddm.lib().ddm_batch_match(ctx, 2, 0, None, None, None, 0, None, None, None, 0, 0, None, 0,
                                    None, None, None)
     assert rc == ddm.DDM_ERR_ARG
+
+
+def test_batched_workload_exact(ctx):
+    """The batched workload itself (4,096 independent d = 2 problems, sizes
+    log-uniform in [1e2, 1e5], 5.8e7 extents): every instance's per-update
+    counts and order-independent digests equal the oracle's, and 40
+    instances match pair by pair."""
+    from tests.helpers import digests_from_pairs
+    inst = W.batched_instances(4096, d=2, alpha=1.0, size_lo=100, size_hi=100_000, seed=0)
+    K, p, po, _ = run_batch(ctx, inst)
+    threads = oracle.threads()
+    sample = set(np.random.default_rng(4).choice(len(inst), 40, replace=False).tolist())
+    total = 0
+    for i, a in enumerate(inst):
+        got = p[po[i]:po[i + 1]]
+        m_i = a[0].shape[1]
+        Ko, counts, digests = oracle.itm_count(*a, threads=threads)
+        total += Ko
+        assert len(got) == Ko, i
+        gc = np.bincount(got[:, 0], minlength=m_i).astype(np.uint32)
+        assert np.array_equal(gc, counts), i
+        assert (np.diff(got[:, 0].astype(np.int64)) >= 0).all()      # grouped by update
+        off = np.concatenate([[0], np.cumsum(gc, dtype=np.int64)])
+        assert np.array_equal(digests_from_pairs(off, got[:, 1]), digests), i
+        if i in sample:
+            _, ou, os_ = oracle.itm_pairs(*a)
+            assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(ou, os_))), i
+    assert total == K == 58345727

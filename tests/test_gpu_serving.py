@@ -158,3 +158,56 @@ def test_pair_offsets_of_concatenated_sets():
             assert np.all((sl >= bounds[i]) & (sl < bounds[i + 1]))
     finally:
         ddm.ddm_destroy(ctx)
+
+
+def test_serving_scale_requests_exact():
+    """The serving workload's scale: 1e6 resident regions (d = 2, side 1e3)
+    moving every 2 ms, requests of 1e3 .. 2e5 updates admitted together;
+    every request's pairs equal a fresh match against the version it pinned,
+    and four of them equal the oracle's."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    d, n, l = 2, 1_000_000, 1000.0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(2026)
+    lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
+    hi = (lo + l).contiguous()
+    regions = S.ResidentRegions(lo, hi, keep_history=True, rebuild_every=1)
+    state = {"lo": lo, "hi": hi}
+    mg = torch.Generator(device="cuda")
+    mg.manual_seed(5)
+
+    def mover(step):
+        state["lo"], state["hi"] = S.random_walk(state["lo"], state["hi"], 1000.0, mg)
+        return state["lo"], state["hi"]
+
+    sched = S.poisson_schedule(rate=2000.0, duration=0.015, federates=64, size_lo=1000,
+                               size_hi=200_000, seed=8)
+    assert len(sched) >= 15
+    srv = S.Server(regions, l, slots=4, pair_capacity=1 << 24, keep_pairs=True)
+    ctx = ddm.ddm_create(0)
+    try:
+        done = srv.run(sched, mover=mover, step_s=0.002)
+        for r in done:
+            plo, phi = regions.history[r.step]
+            ulo, uhi = S.request_updates(r.seed, r.size, d, l)
+            K = ddm.ddm_count(ctx, ulo, uhi, plo, phi)
+            assert K == r.K
+            buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+            ddm.ddm_match(ctx, ulo, uhi, plo, phi, buf)
+            alone = buf[:K].cpu().numpy().view(np.uint32)
+            assert np.array_equal(np.sort(keys(r.pairs[:, 0], r.pairs[:, 1])),
+                                  np.sort(keys(alone[:, 0], alone[:, 1])))
+        for r in sorted(done, key=lambda r: r.size)[-4:]:
+            plo, phi = regions.history[r.step]
+            ulo, uhi = S.request_updates(r.seed, r.size, d, l)
+            Ko, ou, os_ = oracle.itm_pairs(ulo.cpu().numpy(), uhi.cpu().numpy(),
+                                           plo.cpu().numpy(), phi.cpu().numpy())
+            assert Ko == r.K
+            assert np.array_equal(np.sort(keys(r.pairs[:, 0], r.pairs[:, 1])),
+                                  np.sort(keys(ou, os_)))
+    finally:
+        srv.close()
+        ddm.ddm_destroy(ctx)
+        regions.close()
