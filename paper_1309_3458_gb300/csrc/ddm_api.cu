@@ -227,7 +227,7 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
   DDM_CUDA(launch_validate_batch(d, lo, hi, cnt, bs.inst,
                                  static_cast<unsigned long long*>(c->keys[0].p),
                                  static_cast<uint32_t*>(c->vals[0].p), aos, c->st_dev, c->sms, s));
-  DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(bs.count ? bs.count - 1 : 0), cur, s));
+  DDM_TRY(sort_pass(c, cnt, 3 + key_bytes(bs.count ? bs.count - 1 : 0), cur, s));
   for (int k = 1; k < d; ++k) {
     auto* gl = static_cast<int*>(c->bglog2.p);
     auto* ng = static_cast<uint32_t*>(c->bngroups.p);
@@ -237,7 +237,7 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
     DDM_CUDA(launch_rekey_batch(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt,
                                 cnt, bs.inst, bs.off, gl, gb,
                                 static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
-    DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(cnt), cur, s));  // at most cnt groups
+    DDM_TRY(sort_pass(c, cnt, 3 + key_bytes(cnt), cur, s));  // at most cnt groups
   }
   return DDM_OK;
 }
@@ -265,7 +265,7 @@ int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint3
   DDM_CUDA(launch_validate_class(d, lo, hi, cnt, static_cast<unsigned long long*>(c->keys[0].p),
                                  static_cast<uint32_t*>(c->vals[0].p), hist, aos, c->st_dev,
                                  c->sms, s));
-  DDM_TRY(sort_pass(c, cnt, 8, cur, s));
+  DDM_TRY(sort_pass(c, cnt, 4, cur, s));  // (class, 24-bit lower bound)
   DDM_CUDA(launch_scan(hist, kClasses, off, sums, nullptr, s));
   DDM_CUDA(launch_fill_inst(off, kClasses, cnt, inst, c->sms, s));
   for (int k = 1; k < d; ++k) {
@@ -277,7 +277,7 @@ int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint3
     DDM_CUDA(launch_rekey_batch(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt,
                                 cnt, inst, off, gl, gb,
                                 static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
-    DDM_TRY(sort_pass(c, cnt, 4 + key_bytes(cnt), cur, s));  // at most cnt groups
+    DDM_TRY(sort_pass(c, cnt, 3 + key_bytes(cnt), cur, s));  // at most cnt groups
   }
   return DDM_OK;
 }
@@ -289,7 +289,7 @@ int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
   DDM_CUDA(launch_validate(d, lo, hi, cnt, static_cast<unsigned long long*>(c->keys[0].p),
                            static_cast<uint32_t*>(c->vals[0].p), tree ? 1 : 2, aos, c->st_dev,
                            c->sms, s));
-  DDM_TRY(sort_pass(c, cnt, tree ? 8 : 4, cur, s));
+  DDM_TRY(sort_pass(c, cnt, tree ? 8 : 3, cur, s));
   int glog2[DDM_MAX_DIMS];
   str_groups(cnt, d, glog2, c->str_shift);
   for (int k = 1; k < d; ++k) {
@@ -298,7 +298,7 @@ int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
                           glog2[k], static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
     int gbits = 0;
     while (gbits < 32 && (((uint64_t)(cnt - 1) >> glog2[k]) >> gbits) != 0) ++gbits;
-    DDM_TRY(sort_pass(c, cnt, 4 + (gbits + 7) / 8, cur, s));
+    DDM_TRY(sort_pass(c, cnt, 3 + (gbits + 7) / 8, cur, s));
   }
   return DDM_OK;
 }

@@ -2,11 +2,12 @@
 //
 // Every extent must have lo <= hi with no NaN in every dimension (the
 // paper's segments [low, high], Section III-A); a violation raises
-// kErrExtent.  For the subscription set the same pass emits the 64-bit sort
-// key of the interval tree order of Section IV -- lower bound, ties broken
-// by upper bound -- as (key(lo0) << 32 | key(hi0)), and the identity id
-// payload, so a stable radix sort leaves remaining ties in id order.  The
-// update set only needs a locality order: its key is key(lo0) alone.
+// kErrExtent.  For the subscription set of a d = 1 tree the same pass emits
+// the 64-bit sort key of the interval tree order of Section IV -- lower
+// bound, ties broken by upper bound -- as (key(lo0) << 32 | key(hi0)), and
+// the identity id payload, so a stable radix sort leaves remaining ties in id
+// order.  Every other order (d > 1 trees, the updates) is a locality order:
+// its keys hold the top 24 bits of key(lo) below a class, group or instance.
 //
 // For d > 1 the order is then refined one dimension at a time: inside
 // aligned groups of consecutive positions the extents are re-sorted by their
@@ -24,6 +25,13 @@ namespace ddm {
 namespace {
 
 constexpr int kThreads = 256;
+// Locality keys (every sort but the d = 1 tree's): the top 24 bits of the
+// order-preserving float key -- sign, exponent and 15 mantissa bits, about
+// 3e-5 relative -- below a group / class / instance number.  Such an order
+// is a heuristic (any order gives the same pairs), and dropping the low
+// byte saves one radix pass per sort.
+constexpr int kLocalityBits = 24;
+constexpr int kLocalityDrop = 32 - kLocalityBits;
 
 __global__ void __launch_bounds__(kThreads)
 k_validate(int d, const float* __restrict__ lo, const float* __restrict__ hi, uint32_t cnt,
@@ -42,7 +50,7 @@ k_validate(int d, const float* __restrict__ lo, const float* __restrict__ hi, ui
     if (keys) {
       const float a = __ldg(lo + i), b = __ldg(hi + i);
       keys[i] = key_mode == 1 ? ((unsigned long long)float_key(a) << 32) | float_key(b)
-                              : (unsigned long long)float_key(a);
+                              : (unsigned long long)(float_key(a) >> kLocalityDrop);
       vals[i] = i;
     }
   }
@@ -54,7 +62,8 @@ k_rekey(const uint32_t* __restrict__ vals, const float* __restrict__ lo_k, uint3
         unsigned long long* __restrict__ keys) {
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride)
-    keys[i] = ((unsigned long long)(i >> glog2) << 32) | float_key(__ldg(lo_k + vals[i]));
+    keys[i] = ((unsigned long long)(i >> glog2) << kLocalityBits) |
+              (float_key(__ldg(lo_k + vals[i])) >> kLocalityDrop);
 }
 
 __global__ void __launch_bounds__(kThreads)
@@ -98,9 +107,8 @@ k_validate_class(int d, const float* __restrict__ lo, const float* __restrict__ 
       if (aos) aos[(size_t)i * d + k] = make_float2(a, b);
     }
     const uint32_t cls = (__float_as_uint(side) >> 23) & 0xffu;
-    keys[i] = ((unsigned long long)cls << 56) |
-              ((unsigned long long)float_key(__ldg(lo + i)) << 24) |
-              (unsigned long long)(float_key(__ldg(hi + i)) >> 8);
+    keys[i] = ((unsigned long long)cls << kLocalityBits) |
+              (float_key(__ldg(lo + i)) >> kLocalityDrop);
     vals[i] = i;
     atomicAdd(&s_h[cls], 1u);
   }
@@ -140,7 +148,8 @@ k_validate_batch(int d, const float* __restrict__ lo, const float* __restrict__ 
       bad |= !(a <= b);
       if (aos) aos[(size_t)i * d + k] = make_float2(a, b);
     }
-    keys[i] = ((unsigned long long)inst[i] << 32) | float_key(__ldg(lo + i));
+    keys[i] = ((unsigned long long)inst[i] << kLocalityBits) |
+              (float_key(__ldg(lo + i)) >> kLocalityDrop);
     vals[i] = i;
   }
   if (__ballot_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&st->err, kErrExtent);
@@ -172,7 +181,7 @@ k_rekey_batch(const uint32_t* __restrict__ vals, const float* __restrict__ lo_k,
     const uint32_t b = inst[i];
     const unsigned long long local = i - off[b];
     const unsigned long long group = gbase[b] + (local >> glog2[b]);
-    keys[i] = (group << 32) | float_key(__ldg(lo_k + vals[i]));
+    keys[i] = (group << kLocalityBits) | (float_key(__ldg(lo_k + vals[i])) >> kLocalityDrop);
   }
 }
 

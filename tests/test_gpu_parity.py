@@ -165,13 +165,14 @@ def test_tree_order_and_node_bounds(ctx):
             pos += c
     # Order for d >= 2: size classes ascending (the binary exponent of each
     # extent's largest side), and inside a class the dimension-0 lower bounds
-    # ascend from one re-sort group to the next (aligned powers of two counted
-    # from the class's first position).
+    # -- to the 24 bits the locality keys keep -- ascend from one re-sort
+    # group to the next (aligned powers of two counted from the class's first
+    # position).
     side = (arrays[3] - arrays[2]).max(axis=0)          # float32, as on the device
     cls = (side.view(np.uint32) >> 23) & 0xff
     c_ord = cls[order]
     assert (np.diff(c_ord.astype(np.int64)) >= 0).all()
-    lo0 = arrays[2][0][order]
+    lo0 = (order_key(arrays[2][0]) >> np.uint32(8))[order].astype(np.float64)
     for c in np.unique(c_ord):
         pos = np.nonzero(c_ord == c)[0]
         start, cnt = int(pos[0]), len(pos)
@@ -179,9 +180,16 @@ def test_tree_order_and_node_bounds(ctx):
         seg = lo0[start:start + cnt]
         nb = -(-cnt // G)
         pad = nb * G - cnt
-        bmax = np.concatenate([seg, np.full(pad, -np.inf, np.float32)]).reshape(nb, G).max(1)
-        bmin = np.concatenate([seg, np.full(pad, np.inf, np.float32)]).reshape(nb, G).min(1)
+        bmax = np.concatenate([seg, np.full(pad, -np.inf)]).reshape(nb, G).max(1)
+        bmin = np.concatenate([seg, np.full(pad, np.inf)]).reshape(nb, G).min(1)
         assert (bmax[:-1] <= bmin[1:]).all()
+
+
+def order_key(x):
+    """IEEE order as unsigned integers (-0 like +0): the sort keys' mapping."""
+    b = np.ascontiguousarray(x, dtype=np.float32).view(np.uint32).copy()
+    b[b == np.uint32(0x80000000)] = 0
+    return np.where(b & np.uint32(0x80000000), ~b, b | np.uint32(0x80000000)).astype(np.uint32)
 
 
 def str_group_log2(n, d, k):
