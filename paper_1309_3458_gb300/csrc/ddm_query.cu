@@ -465,10 +465,14 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
          uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
          uint32_t* __restrict__ work, Status* __restrict__ st) {
   using Cursor = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-  __shared__ uint4 s_rec[kWarps][32];   // leaf, hit mask, update id, subscription id base
-  __shared__ Cursor s_at[kWarps][32];   // output position of the record's first pair
+  // Per record: leaf, hit mask, update id, and the output position of its first
+  // pair (32-bit positions, not batched: one 128-bit load per record) or else
+  // the subscription id base, the position then in s_at.
+  __shared__ uint4 s_rec[kWarps][32];
+  __shared__ Cursor s_at[kWarps][32];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t below = (1u << lane) - 1u;  // lanes below this one
+  const uint32_t lanebit = 1u << lane;
   if (!records_complete(ra)) return;  // the walking write pass handles this range
   const unsigned long long base0 = w.start[w.b_idx];
   const unsigned long long need = w.start[w.e_idx] - base0;
@@ -531,29 +535,29 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
       const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
       const uint32_t sb = BATCH ? __shfl_sync(0xffffffffu, sub_base, qq) : 0u;
       __syncwarp();  // the previous round has read s_rec / s_at
-      s_rec[wib][lane] = make_uint4(x >> 5, hb, Qq, sb);
-      s_at[wib][lane] = o;
+      constexpr bool kPacked = !WIDE && !BATCH;  // position fits the record's fourth word
+      s_rec[wib][lane] = make_uint4(x >> 5, hb, Qq, kPacked ? (uint32_t)o : sb);
+      if (!kPacked) s_at[wib][lane] = o;
       __syncwarp();
 #pragma unroll 1
       for (int g = 0; g < 32; g += 8) {
-        uint32_t hr[8], sv[8];
+        uint4 rr[8];
+        uint32_t sv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const uint2 a = *reinterpret_cast<const uint2*>(&s_rec[wib][g + u]);
-          hr[u] = a.y;
+          rr[u] = s_rec[wib][g + u];
           sv[u] = 0u;
-          if ((hr[u] >> lane) & 1u) sv[u] = ld_hinted(sid + a.x * 32u + (uint32_t)lane, keep);
+          if (rr[u].y & lanebit) sv[u] = ld_hinted(sid + rr[u].x * 32u + (uint32_t)lane, keep);
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const uint4 a = s_rec[wib][g + u];
-          const Cursor at = s_at[wib][g + u];
-          if ((hr[u] >> lane) & 1u) {
+          if (rr[u].y & lanebit) {
+            const Cursor at = kPacked ? (Cursor)rr[u].w : s_at[wib][g + u];
             ddm_pair pr;
-            pr.upd = a.z;
-            pr.sub = sv[u] - a.w;
+            pr.upd = rr[u].z;
+            pr.sub = sv[u] - (kPacked ? 0u : rr[u].w);
             if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
-            st_hinted(pairs + (unsigned long long)(at + (Cursor)__popc(hr[u] & below)), pr, stream);
+            st_hinted(pairs + (unsigned long long)(at + (Cursor)__popc(rr[u].y & below)), pr, stream);
           }
         }
       }
