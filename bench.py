@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--serving-only", action="store_true", help="run only the serving run")
     ap.add_argument("--serving-seconds", type=float, default=2.0)
     ap.add_argument("--no-sweep", action="store_true", help="skip the alpha x N sweep")
+    ap.add_argument("--no-compressed", action="store_true",
+                    help="skip the compressed-output (subscription ids by column) runs")
     ap.add_argument("--phase", default="all", choices=["all", "build"],
                     help="build: time ddm_build alone (sort + tree) on the workload's "
                          "subscriptions, for profiling the build kernels")
@@ -673,6 +675,64 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
+    # ---- compressed output (Section II: M stored by columns) ----
+    # The same step, writing only each pair's subscription id (4 bytes) into
+    # the same device buffer, plus the plan order (the update of each column)
+    # and the column offsets.
+    ids_all = pairs.view(-1)
+    cap_ids = ids_all.shape[0]
+    order_d = torch.empty(m, dtype=torch.int32, device="cuda")
+    ooff_d = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    compressed = None
+    if not args.no_compressed:
+        cw_ms, cw_bytes, cw_ids = [], [], []
+
+        def step_ids(c, record=False, cap_c=cap_ids, buf=ids_all):
+            ddm.ddm_build(c, dev[2], dev[3])
+            Kc = ddm.ddm_plan(c, dev[0], dev[1])
+            ddm.ddm_plan_order(c, order_d, ooff_d)
+            b = 0
+            while b < m:
+                e = ddm.ddm_chunk_end_ordered(c, b, cap_c)
+                if record:
+                    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    s0.record(stream)
+                k = ddm.ddm_write_ordered_ids(c, b, e, buf)
+                if record:
+                    s1.record(stream)
+                    cw_ms.append((s0, s1))
+                    cw_bytes.append(8 * d * (e - b) + 8 * d * n + 4 * k)
+                    cw_ids.append(k)
+                b = e
+            return Kc
+
+        for _ in range(args.warmup):
+            step_ids(ctx)
+        torch.cuda.synchronize()
+        barrier()
+        c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        c0.record(stream)
+        for _ in range(args.steps):
+            Kc = step_ids(ctx, record=True)
+        c1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        c_s = c0.elapsed_time(c1) / 1e3
+        t_c, k_c = job_totals(c_s, Kc * args.steps, world, device="cuda")
+        cws = sum(a.elapsed_time(b) for a, b in cw_ms) / 1e3
+        c_gbs = sum(cw_bytes) / cws / 1e9 if cws > 0 else 0.0
+        compressed = {
+            "value": k_c / t_c,
+            "unit": "pairs/s", "ms_per_step": 1e3 * c_s / args.steps,
+            "write_ms_per_step": 1e3 * cws / args.steps, "K": Kc,
+            "chunks": len(cw_ids) // max(1, args.steps),
+            "output": "subscription ids (uint32) in plan order + plan order (uint32) + column "
+                      "offsets (uint64): the intersection matrix by columns",
+            "roofline": {"bound": "hbm", "kernel": "k_replay (ddm_write_ordered_ids)",
+                         "achieved": c_gbs, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": c_gbs / hbm_peak, "peak_source": peak_src,
+                         "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 4*(ids in chunk)"}}
+
     # ---- end to end with host buffers ----
     # Inputs are copied from pinned host memory every step and every pair is
     # copied back to pinned host memory.  The device pair buffer is split in
@@ -680,7 +740,7 @@ def main():
     # the next chunk is written into the other half.  Two contexts alternate
     # between steps, so that a step's build and count run while the previous
     # step's last pairs are still being copied out.
-    e2e = None
+    e2e = e2e_compressed = None
     if not args.no_e2e:
         host = [torch.from_numpy(a).pin_memory() for a in arrays]
         stage = torch.empty((int(args.stage_gb * 1e9) // 8, 2), dtype=torch.int32).pin_memory()
@@ -688,12 +748,17 @@ def main():
         e2e_steps = args.e2e_steps or max(1, min(args.steps, 3))
         half = cap // 2
         bufs = (pairs[:half], pairs[half:2 * half])
+        half_ids = cap_ids // 2
+        bufs_ids = (ids_all[:half_ids], ids_all[half_ids:2 * half_ids])
+        stage_ids = stage.view(-1)
+        order_h = torch.empty(m, dtype=torch.int32).pin_memory()
+        ooff_h = torch.empty(m + 1, dtype=torch.int64).pin_memory()
         copy_stream = torch.cuda.Stream()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         ctxs = (ctx, ddm.ddm_create(local))
         chunk_no = [0]
 
-        def e2e_run(nsteps):
+        def e2e_run(nsteps, ids=False):
             Ke = 0
             for st in range(nsteps):
                 c = ctxs[st % 2]
@@ -701,21 +766,32 @@ def main():
                     t_dev.copy_(t_host, non_blocking=True)
                 ddm.ddm_build(c, dev[2], dev[3])
                 Ke = ddm.ddm_plan(c, dev[0], dev[1])
+                if ids:   # the columns' updates and offsets, then the ids chunk by chunk
+                    stream.wait_event(copied[0])
+                    stream.wait_event(copied[1])
+                    ddm.ddm_plan_order(c, order_d, ooff_d)
+                    planned = torch.cuda.Event()
+                    planned.record(stream)
+                    copy_stream.wait_event(planned)
+                    with torch.cuda.stream(copy_stream):
+                        order_h.copy_(order_d, non_blocking=True)
+                        ooff_h.copy_(ooff_d, non_blocking=True)
                 b = 0
                 while b < m:
-                    e = ddm.ddm_chunk_end_ordered(c, b, half)
+                    e = ddm.ddm_chunk_end_ordered(c, b, half_ids if ids else half)
                     i = chunk_no[0]
-                    buf = bufs[i % 2]
+                    buf = (bufs_ids if ids else bufs)[i % 2]
                     stream.wait_event(copied[i % 2])      # that half's previous pairs are out
-                    k = ddm.ddm_write_ordered(c, b, e, buf)
+                    k = (ddm.ddm_write_ordered_ids if ids else ddm.ddm_write_ordered)(c, b, e, buf)
                     written = torch.cuda.Event()
                     written.record(stream)
                     copy_stream.wait_event(written)
+                    st_buf = stage_ids if ids else stage
                     with torch.cuda.stream(copy_stream):
                         o = 0
                         while o < k:
-                            n_c = min(stage.shape[0], k - o)
-                            stage[:n_c].copy_(buf[o:o + n_c], non_blocking=True)
+                            n_c = min(st_buf.shape[0], k - o)
+                            st_buf[:n_c].copy_(buf[o:o + n_c], non_blocking=True)
                             o += n_c
                         copied[i % 2].record(copy_stream)
                     b, chunk_no[0] = e, i + 1
@@ -739,6 +815,21 @@ def main():
         e2e = {"value": Ke * e2e_steps / te * (world if world > 1 else 1), "unit": "pairs/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(8 * Ke),
                "steps": e2e_steps}
+        if not args.no_compressed:
+            e2e_run(1, ids=True)
+            barrier()
+            torch.cuda.synchronize()
+            e0.record(stream)
+            Ke = e2e_run(e2e_steps, ids=True)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            barrier()
+            te = e0.elapsed_time(e1) / 1e3
+            e2e_compressed = {
+                "value": Ke * e2e_steps / te * (world if world > 1 else 1), "unit": "pairs/s",
+                "h2d_bytes_per_step": int(h2d),
+                "d2h_bytes_per_step": int(4 * Ke + order_h.nbytes + ooff_h.nbytes),
+                "steps": e2e_steps, "output": "compressed (ids by column)"}
         ddm.ddm_destroy(ctxs[1])
         del host, stage
 
@@ -807,6 +898,8 @@ def main():
             "write": 1e3 * write_s / args.steps,
             "count_bound": "alu (issue-bound tree walk, see profiles/)"},
         "e2e": e2e,
+        "compressed": compressed,
+        "e2e_compressed": e2e_compressed,
         "gpu_launches": int(launches),
         "cpu_baseline": cpu,
         "clocks": clocks,

@@ -277,7 +277,24 @@ int ddm_plan_order(ddm_ctx *ctx, uint32_t *order, uint64_t *order_offsets, void 
 int ddm_write_ordered(ddm_ctx *ctx, uint32_t pos_begin, uint32_t pos_end,
                       ddm_pair *pairs, uint64_t capacity, uint64_t *k_out, void *stream);
 
-/* Chunk planning for ddm_write_ordered: *pos_end = the largest e <= m such
+/* Compressed output (Section II: the intersection matrix M is sparse and
+ * can be stored in compressed form).  Writes what ddm_write_ordered writes
+ * for plan positions pos_begin <= p < pos_end, but only the subscription id
+ * of each pair (uint32; instance-local when batched), at the same index:
+ * sub_ids[0 .. order_offsets[pos_end] - order_offsets[pos_begin]).  With
+ * ddm_plan_order's order (the update at each plan position) and
+ * order_offsets (where each position's ids start) this is M stored by
+ * columns, one column per update holding the ids of the subscriptions it
+ * overlaps, in half the bytes of the pair list.  capacity counts ids.
+ * *k_out = the id count; DDM_ERR_CAPACITY (nothing written) if it exceeds
+ * capacity.  Each id is an index into the set the tree was built over
+ * (DDM_SWAP_ROLES does not apply).  Synchronises `stream`.  Errors as
+ * ddm_write_ordered. */
+int ddm_write_ordered_ids(ddm_ctx *ctx, uint32_t pos_begin, uint32_t pos_end,
+                          uint32_t *sub_ids, uint64_t capacity, uint64_t *k_out, void *stream);
+
+/* Chunk planning for ddm_write_ordered (and ddm_write_ordered_ids, whose
+ * capacity counts ids): *pos_end = the largest e <= m such
  * that the pairs of plan positions [pos_begin, e) fit in `capacity`;
  * DDM_ERR_CAPACITY with *pos_end = pos_begin when position pos_begin alone
  * does not fit.  Synchronises `stream`. */

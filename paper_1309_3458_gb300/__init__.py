@@ -63,6 +63,7 @@ SIGNATURES = {
     "ddm_chunk_end": (_i, [_vp, _u32, _u64, _pu32, _vp]),
     "ddm_plan_order": (_i, [_vp, _vp, _vp, _vp]),
     "ddm_write_ordered": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
+    "ddm_write_ordered_ids": (_i, [_vp, _u32, _u32, _vp, _u64, _pu64, _vp]),
     "ddm_chunk_end_ordered": (_i, [_vp, _u32, _u64, _pu32, _vp]),
     "ddm_tree_shape": (_i, [_vp, _pi, _pu32, _pu32]),
     "ddm_tree_export": (_i, [_vp, _vp, _vp, _vp, _vp]),
@@ -179,6 +180,17 @@ def _pairs(pairs) -> int:
         raise TypeError("pairs must be an int32 tensor of shape (capacity, 2)")
     _device_tensor(pairs, "pairs")
     return pairs.shape[0]
+
+
+def _ids(ids) -> int:
+    """Capacity of a subscription-id buffer: a 1-D int32 tensor."""
+    import torch
+    if ids is None:
+        return 0
+    if ids.dtype != torch.int32 or ids.dim() != 1:
+        raise TypeError("sub_ids must be a 1-D int32 tensor")
+    _device_tensor(ids, "sub_ids")
+    return ids.shape[0]
 
 
 def _check(rc: int, where: str, k: Optional[int] = None):
@@ -326,6 +338,17 @@ def ddm_write_ordered(ctx: int, pos_begin: int, pos_end: int, pairs, stream=None
     rc = lib().ddm_write_ordered(ctx, pos_begin, pos_end, _ptr(pairs), cap, ctypes.byref(k),
                                  _stream(stream))
     _check(rc, "ddm_write_ordered", k.value)
+    return k.value
+
+
+def ddm_write_ordered_ids(ctx: int, pos_begin: int, pos_end: int, sub_ids, stream=None) -> int:
+    """Compressed output: the subscription ids of ddm_write_ordered's pairs
+    (same positions) into a 1-D int32 tensor; returns the id count."""
+    cap = _ids(sub_ids)
+    k = ctypes.c_uint64(0)
+    rc = lib().ddm_write_ordered_ids(ctx, pos_begin, pos_end, _ptr(sub_ids), cap,
+                                     ctypes.byref(k), _stream(stream))
+    _check(rc, "ddm_write_ordered_ids", k.value)
     return k.value
 
 

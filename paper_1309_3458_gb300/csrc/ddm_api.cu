@@ -502,7 +502,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
 
 // Write pass for the plan positions [pb, pe), laid out in plan order.
 int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, uint64_t capacity,
-                        cudaStream_t s) {
+                        cudaStream_t s, uint32_t* ids = nullptr) {
   if (pe > pb && c->tree.n > 0) {
     QueryView q = query_view(c);
     q.first = pb;
@@ -513,6 +513,7 @@ int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, u
     w.b_idx = pb;
     w.e_idx = pe;
     w.pairs = pairs;
+    w.ids = ids;
     w.capacity = capacity;
     auto* work = static_cast<uint32_t*>(c->work.p);
     if (c->arena.max_blocks)
@@ -783,6 +784,21 @@ int ddm_write_ordered(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, ddm_pair
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(write_ordered_async(c, pos_begin, pos_end, pairs, capacity, s));
+  DDM_TRY(sync_status(c, s));
+  if (k_out) *k_out = c->st_host->K;
+  return status_code(*c->st_host);
+}
+
+int ddm_write_ordered_ids(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, uint32_t* sub_ids,
+                          uint64_t capacity, uint64_t* k_out, void* stream) {
+  if (!c) return DDM_ERR_ARG;
+  if (!c->planned) return DDM_ERR_STATE;
+  if (pos_begin > pos_end || pos_end > c->m || (pos_end > pos_begin && !sub_ids)) return DDM_ERR_ARG;
+  DeviceGuard g(c->device);
+  if (!g.ok()) return DDM_ERR_CUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  DDM_TRY(reset_status(c, s));
+  DDM_TRY(write_ordered_async(c, pos_begin, pos_end, nullptr, capacity, s, sub_ids));
   DDM_TRY(sync_status(c, s));
   if (k_out) *k_out = c->st_host->K;
   return status_code(*c->st_host);

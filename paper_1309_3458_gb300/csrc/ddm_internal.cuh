@@ -67,6 +67,7 @@ struct WriteView {
   const uint32_t* qids;  // optional: id written for query q is qids[q] (else q)
   uint32_t b_idx, e_idx;
   ddm_pair* pairs;
+  uint32_t* ids;  // when set: only each pair's subscription id is written, here, and pairs is unused
   unsigned long long capacity;
 };
 

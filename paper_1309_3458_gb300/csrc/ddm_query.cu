@@ -272,11 +272,15 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
             if (hit) {
               const unsigned long long at = o + __popc(hb & lt);
               if (at < w.capacity) {
-                ddm_pair pr;
-                pr.upd = Qq;
-                pr.sub = my_sid - sub_base;
-                if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
-                w.pairs[at] = pr;
+                if (w.ids) {
+                  w.ids[at] = my_sid - sub_base;
+                } else {
+                  ddm_pair pr;
+                  pr.upd = Qq;
+                  pr.sub = my_sid - sub_base;
+                  if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
+                  w.pairs[at] = pr;
+                }
               }
             }
             if (lane == qq) out = o + __popc(hb);
@@ -443,6 +447,10 @@ __device__ __forceinline__ void st_hinted(ddm_pair* a, ddm_pair v, unsigned long
                : "memory");
 }
 
+__device__ __forceinline__ void st_hinted(uint32_t* a, uint32_t v, unsigned long long policy) {
+  asm volatile("st.global.L2::cache_hint.u32 [%0], %1, %2;" ::"l"(a), "r"(v), "l"(policy) : "memory");
+}
+
 // Write pass from the records of the count pass.  Work unit: one record
 // block (up to 512 records of one packet), taken from the plan-order block
 // list, so uneven packets spread over the whole GPU.  A warp loads the
@@ -458,8 +466,9 @@ __device__ __forceinline__ void st_hinted(ddm_pair* a, ddm_pair v, unsigned long
 // bits -- one contiguous run of the output per record.  Eight records are in
 // flight at a time (their id loads issued before their stores).  Positions
 // are relative to the range's first pair; with fewer than 2^32 pairs in the
-// range (WIDE false) they are 32-bit.
-template <bool FILTER_ID, bool WIDE, bool BATCH>
+// range (WIDE false) they are 32-bit.  IDS: the compressed output, only the
+// subscription id of each pair (4 bytes) at the pair's position.
+template <bool FILTER_ID, bool WIDE, bool BATCH, bool IDS>
 __global__ void __launch_bounds__(kThreads, 4)
 k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uint32_t p0,
          uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
@@ -487,6 +496,7 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
   if (need > w.capacity) return;
   if (!WIDE && need > 0xffffffffull) return;  // host picks WIDE for such ranges
   ddm_pair* __restrict__ pairs = w.pairs;
+  uint32_t* __restrict__ ids = w.ids;
   const uint32_t* __restrict__ sid = t.sid;
   const unsigned long long keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
   const unsigned long long i0 = ra.pkt_off[p0], i1 = ra.pkt_off[p1];
@@ -553,11 +563,17 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
         for (int u = 0; u < 8; ++u) {
           if (rr[u].y & lanebit) {
             const Cursor at = kPacked ? (Cursor)rr[u].w : s_at[wib][g + u];
-            ddm_pair pr;
-            pr.upd = rr[u].z;
-            pr.sub = sv[u] - (kPacked ? 0u : rr[u].w);
-            if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
-            st_hinted(pairs + (unsigned long long)(at + (Cursor)__popc(rr[u].y & below)), pr, stream);
+            const unsigned long long slot = (unsigned long long)(at + (Cursor)__popc(rr[u].y & below));
+            const uint32_t sub = sv[u] - (kPacked ? 0u : rr[u].w);
+            if (IDS) {
+              st_hinted(ids + slot, sub, stream);
+            } else {
+              ddm_pair pr;
+              pr.upd = rr[u].z;
+              pr.sub = sub;
+              if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
+              st_hinted(pairs + slot, pr, stream);
+            }
           }
         }
       }
@@ -610,12 +626,17 @@ void dispatch_replay(bool wide, uint32_t blocks, cudaStream_t s, const TreeView&
                      const QueryView& q, const BatchView& bv, const RecordArena& ra,
                      const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
                      uint32_t idb, uint32_t ide, uint32_t* work, Status* st) {
-  if (wide)
-    k_replay<FILTER_ID, true, BATCH><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe,
-                                                                 idb, ide, work, st);
-  else
-    k_replay<FILTER_ID, false, BATCH><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe,
-                                                                  idb, ide, work, st);
+#define DDM_REPLAY(F, WD, IDS_)                                                              \
+  k_replay<F, WD, BATCH, IDS_><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe, idb, \
+                                                           ide, work, st)
+  if constexpr (!BATCH) {  // compressed output: single problems, position ranges (checked)
+    if (w.ids) {
+      wide ? DDM_REPLAY(false, true, true) : DDM_REPLAY(false, false, true);
+      return;
+    }
+  }
+  wide ? DDM_REPLAY(FILTER_ID, true, false) : DDM_REPLAY(FILTER_ID, false, false);
+#undef DDM_REPLAY
 }
 
 __global__ void k_gather_offsets(const unsigned long long* __restrict__ offsets, uint32_t m,
@@ -657,6 +678,7 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView
                           uint32_t pb, uint32_t pe, bool id_filter, uint32_t idb, uint32_t ide,
                           uint32_t* work, Status* st, int sms, cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
+  if (w.ids && (id_filter || bv.count)) return cudaErrorInvalidValue;  // see dispatch_replay
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
   const uint32_t blocks = (uint32_t)sms * 4u;  // persistent: work = record blocks

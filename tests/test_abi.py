@@ -93,3 +93,9 @@ def test_binding_rejects_host_and_mistyped_arrays():
         ddm.ddm_count(0, lo, hi[:, :4], lo, hi)                 # shapes differ
     with pytest.raises(ValueError):
         ddm.ddm_count(0, lo, hi, lo[:1], hi[:1])                # d differs
+    with pytest.raises(TypeError):
+        ddm.ddm_write_ordered_ids(0, 0, 1, torch.zeros((4, 2), dtype=torch.int32))  # not 1-D
+    with pytest.raises(TypeError):
+        ddm.ddm_write_ordered_ids(0, 0, 1, torch.zeros(4, dtype=torch.int64))       # int64
+    with pytest.raises(ValueError):
+        ddm.ddm_write_ordered_ids(0, 0, 1, torch.zeros(4, dtype=torch.int32))       # host

@@ -308,6 +308,21 @@ def test_ordered_chunks_cover_the_same_pairs(ctx, flags):
     j = int(order[len(order) // 2])
     sel = got[:, 0] == j
     assert np.array_equal(got[sel, 1], ps[off[j]:off[j + 1]])
+    # compressed output (Section II): the subscription ids alone, same chunks
+    # and same positions; with order and ooff it is M stored by columns
+    ids = torch.empty(cap, dtype=torch.int32, device="cuda")
+    got_ids, b = [], 0
+    while b < m:
+        e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
+        k = ddm.ddm_write_ordered_ids(ctx, b, e, ids)
+        assert k == ooff[e] - ooff[b]
+        got_ids.append(ids[:k].cpu().numpy().view(np.uint32).copy())
+        b = e
+    got_ids = np.concatenate(got_ids)
+    assert np.array_equal(got_ids, got[:, 1])
+    cols = np.repeat(order, np.diff(ooff)).astype(np.uint32)
+    _, ou, os_ = oracle.itm_pairs(*arrays, flags=flags)
+    assert np.array_equal(np.sort(keys(cols, got_ids)), np.sort(keys(ou, os_)))
 
 
 def test_replay_and_walking_write_agree(ctx):
@@ -336,6 +351,9 @@ def test_replay_and_walking_write_agree(ctx):
                 a, b = 777, 20001            # a range that starts and ends inside packets
                 part = torch.empty((int(ooff[b] - ooff[a]), 2), dtype=torch.int32, device="cuda")
                 assert ddm.ddm_write_ordered(fresh, a, b, part) == ooff[b] - ooff[a]
+                part_ids = torch.empty(int(ooff[b] - ooff[a]), dtype=torch.int32, device="cuda")
+                assert ddm.ddm_write_ordered_ids(fresh, a, b, part_ids) == ooff[b] - ooff[a]
+                assert torch.equal(part_ids, part[:, 1])
                 sub = torch.empty((K, 2), dtype=torch.int32, device="cuda")
                 ks = ddm.ddm_write(fresh, 3000, 9000, sub)
                 results.append((full, part.cpu().numpy().copy(), sub[:ks].cpu().numpy().copy()))
@@ -384,12 +402,22 @@ def test_capacity_and_state_errors(ctx):
         with pytest.raises(ddm.DDMError) as e:
             ddm.ddm_write(fresh, 0, 1, small)
         assert e.value.code == ddm.DDM_ERR_STATE
+        small_ids = torch.full((K - 1,), -1, dtype=torch.int32, device="cuda")
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_write_ordered_ids(fresh, 0, 1, small_ids)
+        assert e.value.code == ddm.DDM_ERR_STATE
         ddm.ddm_debug_set_alloc_limit(fresh, 1 << 16)
         with pytest.raises(ddm.DDMError) as e:
             ddm.ddm_count(fresh, *U)
         assert e.value.code == ddm.DDM_ERR_NOMEM
         ddm.ddm_debug_set_alloc_limit(fresh, 0)
         assert ddm.ddm_count(fresh, *U) == K
+        ddm.ddm_build(fresh, U[2], U[3])
+        assert ddm.ddm_plan(fresh, U[0], U[1]) == K
+        with pytest.raises(ddm.DDMError) as e:
+            ddm.ddm_write_ordered_ids(fresh, 0, 3000, small_ids)
+        assert e.value.code == ddm.DDM_ERR_CAPACITY and e.value.k == K
+        assert (small_ids == -1).all()  # nothing written when it does not fit
     finally:
         ddm.ddm_destroy(fresh)
     with pytest.raises(ddm.DDMError) as e:
