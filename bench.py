@@ -675,7 +675,7 @@ def main():
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
-    # ---- compressed output (Section II: M stored by columns) ----
+    # ---- compressed output (Section III: M stored by columns) ----
     # The same step, writing only each pair's subscription id (4 bytes) into
     # the same device buffer, plus the plan order (the update of each column)
     # and the column offsets.

@@ -277,7 +277,7 @@ int ddm_plan_order(ddm_ctx *ctx, uint32_t *order, uint64_t *order_offsets, void 
 int ddm_write_ordered(ddm_ctx *ctx, uint32_t pos_begin, uint32_t pos_end,
                       ddm_pair *pairs, uint64_t capacity, uint64_t *k_out, void *stream);
 
-/* Compressed output (Section II: the intersection matrix M is sparse and
+/* Compressed output (Section III: the intersection matrix M is sparse and
  * can be stored in compressed form).  Writes what ddm_write_ordered writes
  * for plan positions pos_begin <= p < pos_end, but only the subscription id
  * of each pair (uint32; instance-local when batched), at the same index:

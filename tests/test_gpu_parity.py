@@ -308,7 +308,7 @@ def test_ordered_chunks_cover_the_same_pairs(ctx, flags):
     j = int(order[len(order) // 2])
     sel = got[:, 0] == j
     assert np.array_equal(got[sel, 1], ps[off[j]:off[j + 1]])
-    # compressed output (Section II): the subscription ids alone, same chunks
+    # compressed output (Section III): the subscription ids alone, same chunks
     # and same positions; with order and ooff it is M stored by columns
     ids = torch.empty(cap, dtype=torch.int32, device="cuda")
     got_ids, b = [], 0
