@@ -466,9 +466,13 @@ __device__ __forceinline__ void st_hinted(uint32_t* a, uint32_t v, unsigned long
 // bits -- one contiguous run of the output per record.  Eight records are in
 // flight at a time (their id loads issued before their stores).  Positions
 // are relative to the range's first pair; with fewer than 2^32 pairs in the
-// range (WIDE false) they are 32-bit.  IDS: the compressed output, only the
-// subscription id of each pair (4 bytes) at the pair's position.
-template <bool FILTER_ID, bool WIDE, bool BATCH, bool IDS>
+// range (WIDE false) they are 32-bit.  OUT fixes the output form at compile
+// time: kOutPairs {update, subscription}; kOutSwapped the same with the
+// fields exchanged (roles swapped: the tree holds the updates); kOutIds the
+// compressed output, only each pair's subscription id (4 bytes) at the
+// pair's position.
+constexpr int kOutPairs = 0, kOutSwapped = 1, kOutIds = 2;
+template <bool FILTER_ID, bool WIDE, bool BATCH, int OUT>
 __global__ void __launch_bounds__(kThreads, 4)
 k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uint32_t p0,
          uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
@@ -565,13 +569,12 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
             const Cursor at = kPacked ? (Cursor)rr[u].w : s_at[wib][g + u];
             const unsigned long long slot = (unsigned long long)(at + (Cursor)__popc(rr[u].y & below));
             const uint32_t sub = sv[u] - (kPacked ? 0u : rr[u].w);
-            if (IDS) {
+            if (OUT == kOutIds) {
               st_hinted(ids + slot, sub, stream);
             } else {
               ddm_pair pr;
-              pr.upd = rr[u].z;
-              pr.sub = sub;
-              if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
+              pr.upd = OUT == kOutSwapped ? sub : rr[u].z;
+              pr.sub = OUT == kOutSwapped ? rr[u].z : sub;
               st_hinted(pairs + slot, pr, stream);
             }
           }
@@ -626,16 +629,22 @@ void dispatch_replay(bool wide, uint32_t blocks, cudaStream_t s, const TreeView&
                      const QueryView& q, const BatchView& bv, const RecordArena& ra,
                      const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
                      uint32_t idb, uint32_t ide, uint32_t* work, Status* st) {
-#define DDM_REPLAY(F, WD, IDS_)                                                              \
-  k_replay<F, WD, BATCH, IDS_><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe, idb, \
-                                                           ide, work, st)
-  if constexpr (!BATCH) {  // compressed output: single problems, position ranges (checked)
+#define DDM_REPLAY(F, WD, OUT)                                                              \
+  k_replay<F, WD, BATCH, OUT><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe, idb, \
+                                                          ide, work, st)
+  // Compressed output and swapped roles: whole single problems only (checked
+  // by launch_replay), so those forms exist for that case alone.
+  if constexpr (!FILTER_ID && !BATCH) {
     if (w.ids) {
-      wide ? DDM_REPLAY(false, true, true) : DDM_REPLAY(false, false, true);
+      wide ? DDM_REPLAY(false, true, kOutIds) : DDM_REPLAY(false, false, kOutIds);
+      return;
+    }
+    if (w.swap) {
+      wide ? DDM_REPLAY(false, true, kOutSwapped) : DDM_REPLAY(false, false, kOutSwapped);
       return;
     }
   }
-  wide ? DDM_REPLAY(FILTER_ID, true, false) : DDM_REPLAY(FILTER_ID, false, false);
+  wide ? DDM_REPLAY(FILTER_ID, true, kOutPairs) : DDM_REPLAY(FILTER_ID, false, kOutPairs);
 #undef DDM_REPLAY
 }
 
@@ -678,7 +687,7 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView
                           uint32_t pb, uint32_t pe, bool id_filter, uint32_t idb, uint32_t ide,
                           uint32_t* work, Status* st, int sms, cudaStream_t s) {
   if (p1 <= p0) return cudaSuccess;
-  if (w.ids && (id_filter || bv.count)) return cudaErrorInvalidValue;  // see dispatch_replay
+  if ((w.ids || w.swap) && (id_filter || bv.count)) return cudaErrorInvalidValue;  // see dispatch_replay
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
   const uint32_t blocks = (uint32_t)sms * 4u;  // persistent: work = record blocks
