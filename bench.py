@@ -40,7 +40,7 @@ DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
 # DRAM bytes (read + write) per pair of the write-pass kernel (k_replay), from
 # the ncu capture summarised in profiles/k_replay_clustered_d3_scale0.15.md
 # (a smaller case of the same workload; traffic scales with pairs written).
-TRAFFIC_PER_PAIR = 9.90
+TRAFFIC_PER_PAIR = 9.83
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
