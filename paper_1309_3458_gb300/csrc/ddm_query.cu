@@ -27,8 +27,10 @@
 // pairs from each update's output offset, or, if the record arena ran out,
 // walks the tree again (k_packets with WRITE), visiting the same leaves in
 // the same order -- either way the pairs come out exactly as counted, in
-// tree order.  Predicates are combined with bitwise ANDs so the per-query
-// test has no branches.
+// tree order.  The write pass can also store only each pair's subscription
+// id (the compressed form of the intersection matrix, Section III), or the
+// pairs with their fields exchanged when the roles are swapped.  Predicates
+// are combined with bitwise ANDs so the per-query test has no branches.
 #include <cfloat>
 #include <type_traits>
 
