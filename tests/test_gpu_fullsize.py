@@ -114,11 +114,15 @@ def test_d3_clustered_full_size_chunked(ctx):
         for p in [p for p in want_pos if b <= p < e]:
             lo_, hi_ = ooff_h[p] - ooff_h[b], ooff_h[p + 1] - ooff_h[b]
             got[want_pos[p]] = buf[lo_:hi_, 1].cpu().numpy().view(np.uint32).copy()
-        if b == 0:   # compressed output at full size: the subscription column, id for id
-            e2 = ddm.ddm_chunk_end_ordered(ctx, 0, int(1e9))
-            sub_ids = torch.empty(int(ooff_h[e2]), dtype=torch.int32, device="cuda")
-            assert ddm.ddm_write_ordered_ids(ctx, 0, e2, sub_ids) == ooff_h[e2] > 5e8
-            assert torch.equal(sub_ids, buf[:int(ooff_h[e2]), 1])
+        if b == 0:
+            # compressed output at full size, more than 2^32 ids in one call (64-bit
+            # positions): the subscription column of the pair list, id for id
+            e2 = ddm.ddm_chunk_end_ordered(ctx, 0, int(4.5e9))
+            k2 = int(ooff_h[e2])
+            assert 2**32 < k2 <= k
+            sub_ids = torch.empty(k2, dtype=torch.int32, device="cuda")
+            assert ddm.ddm_write_ordered_ids(ctx, 0, e2, sub_ids) == k2
+            assert torch.equal(sub_ids, buf[:k2, 1])
             del sub_ids
         b = e
     assert written == K
