@@ -42,6 +42,9 @@
  *    that is dimension-0 lower, upper, id); with DDM_SWAP_ROLES subscription
  *    id ascending, then the updates' tree position.  Only the set of pairs
  *    is the result; the order is deterministic for a given input.
+ *    ddm_write_ordered_ids writes the compressed form instead: only each
+ *    pair's subscription id, with the update of each run given by the plan
+ *    order (Section III: M stored by columns).
  *  - Sizes: 1 <= d <= DDM_MAX_DIMS, n and m <= DDM_MAX_EXTENTS; n == 0 or
  *    m == 0 is valid and gives K = 0.
  *  - A context is not thread safe: one host thread at a time per context.
