@@ -45,7 +45,7 @@ constexpr int kWarps = kThreads / 32;
 // evaluated with the loops swapped (lane = query, loop over the leaf's 32
 // subscriptions), which costs the same whatever the number of queries.
 #ifndef DDM_TRANSPOSE_MIN
-#define DDM_TRANSPOSE_MIN 20
+#define DDM_TRANSPOSE_MIN 24
 #endif
 // Resident 256-thread blocks per SM the packet kernels are compiled for.
 #ifndef DDM_PACKET_MIN_BLOCKS
