@@ -384,6 +384,36 @@ def test_invalid_extents(ctx):
     check_exact(ctx, base)
 
 
+def test_compressed_output_edges(ctx):
+    """Compressed output: empty ranges write nothing (a buffer is not even
+    needed), single plan positions at packet boundaries equal the matching
+    slice of a whole write, and bad ranges are refused."""
+    import torch
+    arrays = W.uniform_fixed_length(5000, 4000, 2, 10.0, seed=7)
+    U = to_dev(arrays)
+    m = 4000
+    ddm.ddm_build(ctx, U[2], U[3])
+    K = ddm.ddm_plan(ctx, U[0], U[1])
+    ooff = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    ddm.ddm_plan_order(ctx, None, ooff)
+    torch.cuda.synchronize()
+    ooff = ooff.cpu().numpy()
+    ids = torch.full((K + 8,), -7, dtype=torch.int32, device="cuda")
+    assert ddm.ddm_write_ordered_ids(ctx, 100, 100, ids) == 0
+    assert ddm.ddm_write_ordered_ids(ctx, m, m, None) == 0
+    assert bool((ids == -7).all())
+    full = torch.empty(K, dtype=torch.int32, device="cuda")
+    assert ddm.ddm_write_ordered_ids(ctx, 0, m, full) == K
+    for p in (0, 31, 32, 33, 2047, m - 1):
+        k = ddm.ddm_write_ordered_ids(ctx, p, p + 1, ids)
+        assert k == ooff[p + 1] - ooff[p]
+        assert torch.equal(ids[:k], full[int(ooff[p]):int(ooff[p + 1])])
+    for b, e in ((10, 5), (0, m + 1)):
+        with pytest.raises(ddm.DDMError) as err:
+            ddm.ddm_write_ordered_ids(ctx, b, e, ids)
+        assert err.value.code == ddm.DDM_ERR_ARG
+
+
 def test_capacity_and_state_errors(ctx):
     import torch
     arrays = W.uniform_fixed_length(3000, 3000, 1, 50.0, seed=3)
