@@ -108,6 +108,7 @@ def lib():
 
 
 def ddm_strerror(code: int) -> str:
+    """Text of a return code."""
     return lib().ddm_strerror(code).decode()
 
 
@@ -199,17 +200,21 @@ def _check(rc: int, where: str, k: Optional[int] = None):
 
 
 def ddm_create(device: int = 0) -> int:
+    """New context on CUDA device `device`; returns its handle."""
     h = ctypes.c_void_p()
     _check(lib().ddm_create(ctypes.byref(h), device), "ddm_create")
     return h.value
 
 
 def ddm_destroy(ctx: int) -> None:
+    """Free a context and all its device memory."""
     _check(lib().ddm_destroy(ctx), "ddm_destroy")
 
 
 def ddm_count(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, flags: int = DDM_CLOSED,
               stream=None) -> int:
+    """K, the number of intersecting (update, subscription) pairs (Algs. 4-5,
+    count only).  Coordinates: float32 device tensors of shape (d, count)."""
     d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_count(ctx, d, ul, uh, m, sl, sh, n, flags, ctypes.byref(k), _stream(stream))
@@ -219,6 +224,8 @@ def ddm_count(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, flags: int = DDM_CLOSED,
 
 def ddm_match(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, pairs, flags: int = DDM_CLOSED,
               stream=None) -> int:
+    """Write all K pairs into `pairs` (int32 device tensor (capacity, 2):
+    update id, subscription id), grouped by update id; returns K."""
     d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
     cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
@@ -230,6 +237,8 @@ def ddm_match(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, pairs, flags: int = DDM_
 
 def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, upd_end: int,
                     pairs, flags: int = DDM_CLOSED, stream=None) -> int:
+    """The pairs of the updates with ids in [upd_begin, upd_end) only (chunked
+    output); returns their count."""
     d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
     cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
@@ -240,11 +249,16 @@ def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, up
 
 
 def ddm_build(ctx: int, sub_lo, sub_hi, stream=None) -> None:
+    """Build the resident tree over the subscriptions (Interval-Tree-Create,
+    Alg. 5); the coordinates are copied."""
     d, sl, sh, n = _set(sub_lo, sub_hi)
     _check(lib().ddm_build(ctx, d, sl, sh, n, _stream(stream)), "ddm_build")
 
 
 def ddm_refit(ctx: int, sub_lo, sub_hi, stream=None) -> None:
+    """Recompute the resident tree's node bounds after its extents moved: same
+    ids and order, new coordinates in sub_lo / sub_hi (d x n float32 device
+    tensors, extent i still at column i; None only for an empty tree)."""
     sl = sh = None
     if sub_lo is not None or sub_hi is not None:
         _, sl, sh, _ = _set(sub_lo, sub_hi)
@@ -252,11 +266,15 @@ def ddm_refit(ctx: int, sub_lo, sub_hi, stream=None) -> None:
 
 
 def ddm_attach(ctx: int, src: int) -> None:
+    """Let `ctx` query the tree built in `src` without copying it."""
     _check(lib().ddm_attach(ctx, src), "ddm_attach")
 
 
 def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
              stream=None) -> int:
+    """Count pass and prefix sum for the updates against the resident tree;
+    optional `offsets` (int64 device tensor, m + 1) receives the per-update
+    output offsets.  Returns K."""
     d, ul, uh, m = _set(upd_lo, upd_hi)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_plan(ctx, ul, uh, m, flags, _arr(offsets, "offsets", 8, m + 1), ctypes.byref(k),
@@ -266,12 +284,15 @@ def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
 
 
 def ddm_plan_async(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, stream=None) -> None:
+    """ddm_plan without host synchronisation (offsets stay in the context)."""
     d, ul, uh, m = _set(upd_lo, upd_hi)
     _check(lib().ddm_plan_async(ctx, ul, uh, m, flags, _stream(stream)), "ddm_plan_async")
 
 
 def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, err_dev=None,
                     stream=None) -> None:
+    """ddm_write without host synchronisation; K and the error bits go to the
+    optional device tensors k_dev (int64, 1) and err_dev (int32, 1)."""
     cap = _pairs(pairs)
     kd, ed = _arr(k_dev, "k_dev", 8, 1), _arr(err_dev, "err_dev", 4, 1)
     _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, kd, ed,
@@ -312,6 +333,8 @@ def ddm_pair_offsets_async(ctx: int, upd_off, pair_off, stream=None) -> None:
 
 
 def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int:
+    """Write the pairs of the current plan's updates with ids in [upd_begin,
+    upd_end), laid out by update id; returns the pair count."""
     cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write(ctx, upd_begin, upd_end, _ptr(pairs), cap, ctypes.byref(k),
@@ -321,6 +344,8 @@ def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int
 
 
 def ddm_chunk_end(ctx: int, upd_begin: int, capacity: int, stream=None) -> int:
+    """Largest update id e such that the pairs of [upd_begin, e) fit in
+    `capacity` pairs."""
     e = ctypes.c_uint32(0)
     rc = lib().ddm_chunk_end(ctx, upd_begin, capacity, ctypes.byref(e), _stream(stream))
     _check(rc, "ddm_chunk_end", e.value)
@@ -328,11 +353,16 @@ def ddm_chunk_end(ctx: int, upd_begin: int, capacity: int, stream=None) -> int:
 
 
 def ddm_plan_order(ctx: int, order=None, order_offsets=None, stream=None) -> None:
+    """The plan's spatial query order: `order` (int32 device tensor, m) gets
+    the update at each plan position, `order_offsets` (int64, m + 1) where each
+    position's pairs start; either may be None."""
     o, oo = _arr(order, "order", 4), _arr(order_offsets, "order_offsets", 8)
     _check(lib().ddm_plan_order(ctx, o, oo, _stream(stream)), "ddm_plan_order")
 
 
 def ddm_write_ordered(ctx: int, pos_begin: int, pos_end: int, pairs, stream=None) -> int:
+    """Write the pairs of plan positions [pos_begin, pos_end), grouped by
+    update in plan order; returns the pair count."""
     cap = _pairs(pairs)
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write_ordered(ctx, pos_begin, pos_end, _ptr(pairs), cap, ctypes.byref(k),
@@ -353,6 +383,8 @@ def ddm_write_ordered_ids(ctx: int, pos_begin: int, pos_end: int, sub_ids, strea
 
 
 def ddm_chunk_end_ordered(ctx: int, pos_begin: int, capacity: int, stream=None) -> int:
+    """Largest plan position e such that the pairs of [pos_begin, e) fit in
+    `capacity` pairs (or ids)."""
     e = ctypes.c_uint32(0)
     rc = lib().ddm_chunk_end_ordered(ctx, pos_begin, capacity, ctypes.byref(e), _stream(stream))
     _check(rc, "ddm_chunk_end_ordered", e.value)
@@ -360,6 +392,7 @@ def ddm_chunk_end_ordered(ctx: int, pos_begin: int, capacity: int, stream=None) 
 
 
 def ddm_tree_shape(ctx: int) -> Tuple[int, Sequence[int], int]:
+    """(levels, node count per level, total nodes) of the resident tree."""
     lv = ctypes.c_int(0)
     cnt = (ctypes.c_uint32 * DDM_MAX_TREE_LEVELS)()
     tot = ctypes.c_uint32(0)
@@ -368,20 +401,26 @@ def ddm_tree_shape(ctx: int) -> Tuple[int, Sequence[int], int]:
 
 
 def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=None) -> None:
+    """Copy out the tree's subscription order (int32, n) and per-level node
+    bounds (float32); any output may be None."""
     _check(lib().ddm_tree_export(ctx, _arr(order, "order", 4), _arr(node_lo, "node_lo", 4),
                                  _arr(node_hi, "node_hi", 4),
                                  _stream(stream)), "ddm_tree_export")
 
 
 def ddm_set_tuning(ctx: int, str_shift: int = 0, ctas_per_sm: int = 8, replay: int = 1) -> None:
+    """Speed-only knobs: re-sort group shift, CTAs per SM of the packet
+    kernels, replay on (1) or off (0).  Results never depend on them."""
     _check(lib().ddm_set_tuning(ctx, str_shift, ctas_per_sm, replay), "ddm_set_tuning")
 
 
 def ddm_set_replay_budget(ctx: int, nbytes: int) -> None:
+    """Upper bound (bytes) of the record arena the count pass may fill."""
     _check(lib().ddm_set_replay_budget(ctx, nbytes), "ddm_set_replay_budget")
 
 
 def ddm_debug_set_alloc_limit(ctx: int, nbytes: int) -> None:
+    """Make device allocations beyond `nbytes` fail (0: no limit), for tests."""
     _check(lib().ddm_debug_set_alloc_limit(ctx, nbytes), "ddm_debug_set_alloc_limit")
 
 
@@ -391,6 +430,7 @@ def ddm_debug_wait_timeout(ctx: int, polls: int, stream=None) -> None:
 
 
 def ddm_debug_launch_count() -> int:
+    """Kernels the library has launched so far in this process."""
     return int(lib().ddm_debug_launch_count())
 
 
