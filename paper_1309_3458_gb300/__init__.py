@@ -401,8 +401,10 @@ def ddm_tree_shape(ctx: int) -> Tuple[int, Sequence[int], int]:
 
 
 def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=None) -> None:
-    """Copy out the tree's subscription order (int32, n) and per-level node
-    bounds (float32); any output may be None."""
+    """Copy out the tree: `order` (int32 device tensor, n) the subscription id
+    at each sorted position; `node_lo` / `node_hi` (float32, d * total) each
+    node's minlower / maxupper per dimension, entry k * total + j, levels
+    stored one after another from level 1.  Any output may be None."""
     _check(lib().ddm_tree_export(ctx, _arr(order, "order", 4), _arr(node_lo, "node_lo", 4),
                                  _arr(node_hi, "node_hi", 4),
                                  _stream(stream)), "ddm_tree_export")
