@@ -58,6 +58,36 @@ def test_argument_errors_without_gpu(lib):
     assert lib.ddm_debug_set_alloc_limit(None, 0) == ddm.DDM_ERR_ARG
 
 
+def test_every_call_refuses_a_null_context_without_gpu(lib):
+    """The remaining entry points check their context (and pointers) on the
+    host before any CUDA call: DDM_ERR_ARG, no GPU needed."""
+    k = ctypes.c_uint64(0)
+    e = ctypes.c_uint32(0)
+    A = ddm.DDM_ERR_ARG
+    assert lib.ddm_match_range(None, 1, None, None, 0, None, None, 0, 0, 0, 0, None, 0,
+                               ctypes.byref(k), None) == A
+    assert lib.ddm_refit(None, None, None, None) == A
+    assert lib.ddm_attach(None, None) == A
+    assert lib.ddm_plan_async(None, None, None, 0, 0, None) == A
+    assert lib.ddm_write_async(None, 0, 0, None, 0, None, None, None) == A
+    assert lib.ddm_pair_offsets_async(None, None, 0, None, None) == A
+    assert lib.ddm_match_moved(None, None, None, 0, None, 0, None, 0, ctypes.byref(k), None) == A
+    assert lib.ddm_plan_stats(None, ctypes.byref(k)) == A
+    assert lib.ddm_plan_order(None, None, None, None) == A
+    assert lib.ddm_write_ordered(None, 0, 0, None, 0, ctypes.byref(k), None) == A
+    assert lib.ddm_write_ordered_ids(None, 0, 0, None, 0, ctypes.byref(k), None) == A
+    assert lib.ddm_chunk_end_ordered(None, 0, 0, ctypes.byref(e), None) == A
+    assert lib.ddm_set_replay_budget(None, 0) == A
+    assert lib.ddm_set_tuning(None, 0, 8, 1) == A
+    assert lib.ddm_debug_wait_timeout(None, 1, None) == A
+    assert lib.ddm_batch_match(None, 1, 1, None, None, None, 0, None, None, None, 0, 0, None, 0,
+                               None, ctypes.byref(k), None) == A
+    assert lib.ddm_batch_match_async(None, 1, 1, None, None, None, 0, None, None, None, 0, 0, None,
+                                     0, None, None, None, None) == A
+    assert lib.ddm_scan_counts_noalloc(None, 0, None, None) == A
+    assert lib.ddm_scan_counts_noalloc(None, ddm.DDM_NOALLOC_MAX_UPDATES + 1, None, None) == A
+
+
 def test_create_reports_missing_device(lib):
     import torch
     if torch.cuda.is_available():
