@@ -31,6 +31,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -120,7 +121,9 @@ class Clocks:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        # raw samples (the JSON line carries their summary); DDM_CLOCKS_DIR keeps them
+        out = os.environ.get("DDM_CLOCKS_DIR") or tempfile.gettempdir()
+        self.path = os.path.join(out, f"ddm_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         try:
