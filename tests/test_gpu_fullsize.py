@@ -10,6 +10,8 @@
   64 GB pair buffer.  Sampled updates are checked pair by pair against brute
   force, a larger sample by count and digest against the oracle's interval
   tree, and properties that hold at any size are checked on every chunk.
+  The compressed output (subscription ids only) of more than 2^32 pairs in
+  one call equals the pair list's subscription column.
 """
 import os
 
