@@ -70,7 +70,7 @@ extern "C" {
 
 /* Flags. */
 #define DDM_CLOSED 0u  /* default: closed segments, x.lo <= y.hi && y.lo <= x.hi */
-#define DDM_OPEN   1u  /* Alg. 1 as printed: x.lo < y.hi && y.lo < x.hi */
+#define DDM_OPEN   1u  /* the strict test of Alg. 1: x.lo < y.hi && y.lo < x.hi */
 /* One-shot calls only (ddm_count, ddm_match, ddm_match_range over the whole
  * update range): build the tree over the UPDATE set and run one query per
  * subscription -- the roles of the two sets swapped, as Section IV allows

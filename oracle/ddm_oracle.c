@@ -50,7 +50,7 @@
 static int intersect_1d(double xlo, double xhi, double ylo, double yhi, int open)
 {
     if (open)
-        return xlo < yhi && ylo < xhi;          /* Alg. 1 as printed */
+        return xlo < yhi && ylo < xhi;          /* the strict test of Alg. 1 */
     return xlo <= yhi && ylo <= xhi;            /* closed segments */
 }
 
@@ -243,32 +243,71 @@ typedef struct {
     uint32_t *out_sub; uint64_t cap; uint64_t K;      /* optional pair list */
 } it_query;
 
-/* Interval-Query (Alg. 4).  Pruning uses maxupper / minlower of the
- * subtree; the node's own interval is tested with Intersect-1D; remaining
- * dimensions 1..d-1 of a dimension-0 hit are tested before reporting. */
-static void it_query_rec(const it_tree *t, int32_t x, it_query *q)
+/* Interval-Query (Alg. 4), written as an iterative in-order walk with an
+ * explicit stack.  Every prune below follows from the segment test of
+ * Section III-A on dimension 0 and from what a subtree's augmented fields
+ * bound:
+ *  - every interval s stored under a node x has s.hi <= x.maxupper and
+ *    s.lo >= x.minlower;
+ *  - s meets the query [ql, qh] (closed rule) only if s.hi >= ql and
+ *    s.lo <= qh, so no interval under x can meet it when x.maxupper < ql or
+ *    x.minlower > qh (these bounds are conservative for the open rule too);
+ *  - the tree is ordered by lower bound, so every interval in x's right
+ *    subtree has s.lo >= x.lo: when x.lo > qh (closed) or x.lo >= qh (open)
+ *    that subtree cannot hold a match.
+ * The walk reports the surviving intervals in tree order (left subtree,
+ * node, right subtree).  An interval that meets the query on dimension 0
+ * is then tested on dimensions 1..d-1 before it is reported. */
+#define IT_STACK_MAX 128   /* AVL height <= 1.45 log2(n + 2) < 64 for n < 2^32 */
+
+static int subtree_may_meet(const it_node *x, double ql, double qh)
 {
-    if (x < 0) return;
-    const it_node *p = &t->v[x];
-    const double ql = q->ulo[q->j], qh = q->uhi[q->j];
-    if (p->maxupper < ql || p->minlower > qh) return;
-    it_query_rec(t, p->left, q);
-    if (intersect_1d(p->lo, p->hi, ql, qh, q->open)) {
-        int ok = 1;
-        for (int k = 1; k < q->d && ok; ++k)
-            ok = intersect_1d(q->slo[(uint64_t)k * q->n + p->id], q->shi[(uint64_t)k * q->n + p->id],
-                              q->ulo[(uint64_t)k * q->m + q->j], q->uhi[(uint64_t)k * q->m + q->j],
-                              q->open);
-        if (ok) {
-            if (q->out_sub && q->K < q->cap) q->out_sub[q->K] = p->id;
-            ++q->K;
-            ++q->count;
-            q->digest += oracle_mix64(p->id);
-        }
+    return !(x->maxupper < ql) && !(x->minlower > qh);
+}
+
+static int right_may_meet(const it_node *x, double qh, int open)
+{
+    return open ? (qh > x->lo) : (qh >= x->lo);
+}
+
+/* Dimensions 1..d-1 of subscription `sid` against the query U_j. */
+static int other_dims_meet(const it_query *q, uint32_t sid)
+{
+    for (int k = 1; k < q->d; ++k) {
+        const uint64_t si = (uint64_t)k * q->n + sid, uj = (uint64_t)k * q->m + q->j;
+        if (!intersect_1d(q->slo[si], q->shi[si], q->ulo[uj], q->uhi[uj], q->open))
+            return 0;
     }
-    /* Right subtree keys have lower >= p->lo. */
-    if (q->open ? (qh > p->lo) : (qh >= p->lo))
-        it_query_rec(t, p->right, q);
+    return 1;
+}
+
+static void it_report(it_query *q, uint32_t sid)
+{
+    if (q->out_sub && q->K < q->cap) q->out_sub[q->K] = sid;
+    ++q->K;
+    ++q->count;
+    q->digest += oracle_mix64(sid);
+}
+
+static void it_query_walk(const it_tree *t, it_query *q)
+{
+    const double ql = q->ulo[q->j], qh = q->uhi[q->j];
+    int32_t stack[IT_STACK_MAX];
+    int top = 0;
+    int32_t x = t->root;
+    for (;;) {
+        /* go down the left spine of every subtree that may hold a match */
+        while (x >= 0 && subtree_may_meet(&t->v[x], ql, qh)) {
+            if (top == IT_STACK_MAX) abort();   /* unreachable for an AVL tree */
+            stack[top++] = x;
+            x = t->v[x].left;
+        }
+        if (top == 0) break;
+        const it_node *p = &t->v[stack[--top]];
+        if (intersect_1d(p->lo, p->hi, ql, qh, q->open) && other_dims_meet(q, p->id))
+            it_report(q, p->id);
+        x = right_may_meet(p, qh, q->open) ? p->right : -1;
+    }
 }
 
 static double now_s(void)
@@ -304,7 +343,7 @@ uint64_t oracle_itm_count(int d,
         q.d = d; q.open = (flags & ORACLE_OPEN) != 0;
         q.ulo = upd_lo; q.uhi = upd_hi; q.m = m; q.j = (uint32_t)jj;
         q.slo = sub_lo; q.shi = sub_hi; q.n = n;
-        it_query_rec(&t, t.root, &q);
+        it_query_walk(&t, &q);
         if (counts) counts[jj] = q.count;
         if (digests) digests[jj] = q.digest;
         K += q.count;
@@ -336,7 +375,7 @@ uint64_t oracle_itm_pairs(int d,
         q.slo = sub_lo; q.shi = sub_hi; q.n = n;
         q.out_sub = out_sub ? out_sub + (K < cap ? K : cap) : NULL;
         q.cap = K < cap ? cap - K : 0;
-        it_query_rec(&t, t.root, &q);
+        it_query_walk(&t, &q);
         if (out_upd)
             for (uint64_t r = K; r < K + q.count && r < cap; ++r) out_upd[r] = j;
         K += q.count;

@@ -19,14 +19,14 @@ import tests.test_oracle as T
 MUTANTS = {
     "closed_rule_strict_low": ("return xlo <= yhi && ylo <= xhi;", "return xlo < yhi && ylo <= xhi;"),
     "bf_drops_dimensions": ("for (int k = 0; k < d; ++k) {", "for (int k = 0; k < 1; ++k) {"),
-    "itm_drops_last_dimension": ("for (int k = 1; k < q->d && ok; ++k)",
-                                 "for (int k = 1; k < q->d - 1 && ok; ++k)"),
-    "right_descent_strict": ("(qh >= p->lo)", "(qh > p->lo)"),
-    "prune_on_equal_upper": ("if (p->maxupper < ql || p->minlower > qh) return;",
-                             "if (p->maxupper <= ql || p->minlower > qh) return;"),
-    "swapped_lo_hi_in_filter": (
-        "ok = intersect_1d(q->slo[(uint64_t)k * q->n + p->id], q->shi[(uint64_t)k * q->n + p->id],",
-        "ok = intersect_1d(q->shi[(uint64_t)k * q->n + p->id], q->slo[(uint64_t)k * q->n + p->id],"),
+    "itm_drops_last_dimension": ("for (int k = 1; k < q->d; ++k) {",
+                                 "for (int k = 1; k < q->d - 1; ++k) {"),
+    "right_descent_strict": ("(qh >= x->lo)", "(qh > x->lo)"),
+    "prune_on_equal_upper": ("!(x->maxupper < ql)", "!(x->maxupper <= ql)"),
+    "prune_on_equal_lower": ("!(x->minlower > qh)", "!(x->minlower >= qh)"),
+    "walk_skips_left_subtrees": ("x = t->v[x].left;", "x = -1;"),
+    "swapped_lo_hi_in_filter": ("intersect_1d(q->slo[si], q->shi[si],",
+                                "intersect_1d(q->shi[si], q->slo[si],"),
     "maxupper_ignores_right_child": ("if (t->v[p->right].maxupper > mu) mu = t->v[p->right].maxupper;",
                                      ";"),
     "rotation_leaves_stale_bounds": ("    t->v[x].right = y;\n    it_fix(t, y);", "    t->v[x].right = y;"),
