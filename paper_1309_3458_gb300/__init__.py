@@ -81,6 +81,11 @@ SIGNATURES = {
 
 _lib = None
 
+# CUDA device of every context this binding created (handle -> device index).
+# The kernels dereference the raw pointers they are given, so a tensor on
+# another GPU than its context must be refused here: the C side cannot tell.
+_CTX_DEVICE = {}
+
 
 class DDMError(RuntimeError):
     """Non-zero return code of a libddm call; ``k`` holds *k_out when set."""
@@ -129,22 +134,32 @@ def _stream(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def _device_tensor(t, what: str):
+def _device_tensor(t, what: str, dev: Optional[int] = None):
     """Kernels read these arrays directly: a host (pageable) pointer would
     fault the GPU, so only CUDA tensors (or pinned host tensors, which the
-    device can address) pass."""
-    if not (getattr(t, "is_cuda", False) or (hasattr(t, "is_pinned") and t.is_pinned())):
+    device can address) pass.  With `dev` given, a CUDA tensor must live on
+    that device: a peer GPU's pointer is not addressable by the kernels."""
+    cuda = bool(getattr(t, "is_cuda", False))
+    if not (cuda or (hasattr(t, "is_pinned") and t.is_pinned())):
         raise ValueError(f"{what} must be a CUDA tensor (or pinned host memory)")
+    if cuda and dev is not None and t.device.index != dev:
+        raise ValueError(f"{what} is on cuda:{t.device.index}, the context on cuda:{dev}")
     if not t.is_contiguous():
         raise ValueError(f"{what} must be contiguous")
 
 
-def _arr(t, what: str, itemsize: int, n: Optional[int] = None):
+def _dev(ctx) -> Optional[int]:
+    """Device of a context made by ddm_create (None for a foreign handle)."""
+    return _CTX_DEVICE.get(ctx)
+
+
+def _arr(t, what: str, itemsize: int, n: Optional[int] = None, dev: Optional[int] = None):
     """Pointer of an optional device array argument (None passes NULL):
-    device-addressable, contiguous, `itemsize`-byte elements, at least `n`."""
+    device-addressable (on `dev` when given), contiguous, `itemsize`-byte
+    elements, at least `n`."""
     if t is None:
         return None
-    _device_tensor(t, what)
+    _device_tensor(t, what, dev)
     if t.element_size() != itemsize:
         raise TypeError(f"{what} must hold {itemsize}-byte elements")
     if n is not None and t.numel() < n:
@@ -152,45 +167,47 @@ def _arr(t, what: str, itemsize: int, n: Optional[int] = None):
     return t.data_ptr()
 
 
-def _set(lo, hi) -> Tuple[int, int, int, int]:
+def _set(lo, hi, dev: Optional[int] = None) -> Tuple[int, int, int, int]:
     import torch
     if lo.dim() != 2 or hi.shape != lo.shape:
         raise ValueError("lo and hi must be (d, count) tensors of the same shape")
     if lo.dtype != torch.float32 or hi.dtype != torch.float32:
         raise TypeError("coordinates must be float32")
-    _device_tensor(lo, "lo")
-    _device_tensor(hi, "hi")
+    _device_tensor(lo, "lo", dev)
+    _device_tensor(hi, "hi", dev)
     d, c = lo.shape
+    if c > DDM_MAX_EXTENTS:  # the C ABI takes a uint32 count
+        raise ValueError(f"{c} extents in one set; at most {DDM_MAX_EXTENTS}")
     return d, _ptr(lo), _ptr(hi), c
 
 
-def _two_sets(upd_lo, upd_hi, sub_lo, sub_hi):
-    d, ul, uh, m = _set(upd_lo, upd_hi)
-    d2, sl, sh, n = _set(sub_lo, sub_hi)
+def _two_sets(upd_lo, upd_hi, sub_lo, sub_hi, dev: Optional[int] = None):
+    d, ul, uh, m = _set(upd_lo, upd_hi, dev)
+    d2, sl, sh, n = _set(sub_lo, sub_hi, dev)
     if d != d2:
         raise ValueError(f"update and subscription sets have {d} and {d2} dimensions")
     return d, ul, uh, m, sl, sh, n
 
 
-def _pairs(pairs) -> int:
+def _pairs(pairs, dev: Optional[int] = None) -> int:
     """Capacity of a pair buffer: an int32 (capacity, 2) tensor."""
     import torch
     if pairs is None:
         return 0
     if pairs.dtype != torch.int32 or pairs.dim() != 2 or pairs.shape[1] != 2:
         raise TypeError("pairs must be an int32 tensor of shape (capacity, 2)")
-    _device_tensor(pairs, "pairs")
+    _device_tensor(pairs, "pairs", dev)
     return pairs.shape[0]
 
 
-def _ids(ids) -> int:
+def _ids(ids, dev: Optional[int] = None) -> int:
     """Capacity of a subscription-id buffer: a 1-D int32 tensor."""
     import torch
     if ids is None:
         return 0
     if ids.dtype != torch.int32 or ids.dim() != 1:
         raise TypeError("sub_ids must be a 1-D int32 tensor")
-    _device_tensor(ids, "sub_ids")
+    _device_tensor(ids, "sub_ids", dev)
     return ids.shape[0]
 
 
@@ -203,19 +220,21 @@ def ddm_create(device: int = 0) -> int:
     """New context on CUDA device `device`; returns its handle."""
     h = ctypes.c_void_p()
     _check(lib().ddm_create(ctypes.byref(h), device), "ddm_create")
+    _CTX_DEVICE[h.value] = device
     return h.value
 
 
 def ddm_destroy(ctx: int) -> None:
     """Free a context and all its device memory."""
     _check(lib().ddm_destroy(ctx), "ddm_destroy")
+    _CTX_DEVICE.pop(ctx, None)
 
 
 def ddm_count(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, flags: int = DDM_CLOSED,
               stream=None) -> int:
     """K, the number of intersecting (update, subscription) pairs (Algs. 4-5,
     count only).  Coordinates: float32 device tensors of shape (d, count)."""
-    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi, _dev(ctx))
     k = ctypes.c_uint64(0)
     rc = lib().ddm_count(ctx, d, ul, uh, m, sl, sh, n, flags, ctypes.byref(k), _stream(stream))
     _check(rc, "ddm_count", k.value)
@@ -226,8 +245,8 @@ def ddm_match(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, pairs, flags: int = DDM_
               stream=None) -> int:
     """Write all K pairs into `pairs` (int32 device tensor (capacity, 2):
     update id, subscription id), grouped by update id; returns K."""
-    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
-    cap = _pairs(pairs)
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi, _dev(ctx))
+    cap = _pairs(pairs, _dev(ctx))
     k = ctypes.c_uint64(0)
     rc = lib().ddm_match(ctx, d, ul, uh, m, sl, sh, n, flags, _ptr(pairs), cap, ctypes.byref(k),
                          _stream(stream))
@@ -239,8 +258,8 @@ def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, up
                     pairs, flags: int = DDM_CLOSED, stream=None) -> int:
     """The pairs of the updates with ids in [upd_begin, upd_end) only (chunked
     output); returns their count."""
-    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
-    cap = _pairs(pairs)
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi, _dev(ctx))
+    cap = _pairs(pairs, _dev(ctx))
     k = ctypes.c_uint64(0)
     rc = lib().ddm_match_range(ctx, d, ul, uh, m, sl, sh, n, upd_begin, upd_end, flags,
                                _ptr(pairs), cap, ctypes.byref(k), _stream(stream))
@@ -251,7 +270,7 @@ def ddm_match_range(ctx: int, upd_lo, upd_hi, sub_lo, sub_hi, upd_begin: int, up
 def ddm_build(ctx: int, sub_lo, sub_hi, stream=None) -> None:
     """Build the resident tree over the subscriptions (Interval-Tree-Create,
     Alg. 5); the coordinates are copied."""
-    d, sl, sh, n = _set(sub_lo, sub_hi)
+    d, sl, sh, n = _set(sub_lo, sub_hi, _dev(ctx))
     _check(lib().ddm_build(ctx, d, sl, sh, n, _stream(stream)), "ddm_build")
 
 
@@ -261,7 +280,7 @@ def ddm_refit(ctx: int, sub_lo, sub_hi, stream=None) -> None:
     tensors, extent i still at column i; None only for an empty tree)."""
     sl = sh = None
     if sub_lo is not None or sub_hi is not None:
-        _, sl, sh, _ = _set(sub_lo, sub_hi)
+        _, sl, sh, _ = _set(sub_lo, sub_hi, _dev(ctx))
     _check(lib().ddm_refit(ctx, sl, sh, _stream(stream)), "ddm_refit")
 
 
@@ -275,9 +294,9 @@ def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
     """Count pass and prefix sum for the updates against the resident tree;
     optional `offsets` (int64 device tensor, m + 1) receives the per-update
     output offsets.  Returns K."""
-    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d, ul, uh, m = _set(upd_lo, upd_hi, _dev(ctx))
     k = ctypes.c_uint64(0)
-    rc = lib().ddm_plan(ctx, ul, uh, m, flags, _arr(offsets, "offsets", 8, m + 1), ctypes.byref(k),
+    rc = lib().ddm_plan(ctx, ul, uh, m, flags, _arr(offsets, "offsets", 8, m + 1, dev=_dev(ctx)), ctypes.byref(k),
                         _stream(stream))
     _check(rc, "ddm_plan", k.value)
     return k.value
@@ -285,7 +304,7 @@ def ddm_plan(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, offsets=None,
 
 def ddm_plan_async(ctx: int, upd_lo, upd_hi, flags: int = DDM_CLOSED, stream=None) -> None:
     """ddm_plan without host synchronisation (offsets stay in the context)."""
-    d, ul, uh, m = _set(upd_lo, upd_hi)
+    d, ul, uh, m = _set(upd_lo, upd_hi, _dev(ctx))
     _check(lib().ddm_plan_async(ctx, ul, uh, m, flags, _stream(stream)), "ddm_plan_async")
 
 
@@ -293,8 +312,8 @@ def ddm_write_async(ctx: int, upd_begin: int, upd_end: int, pairs, k_dev=None, e
                     stream=None) -> None:
     """ddm_write without host synchronisation; K and the error bits go to the
     optional device tensors k_dev (int64, 1) and err_dev (int32, 1)."""
-    cap = _pairs(pairs)
-    kd, ed = _arr(k_dev, "k_dev", 8, 1), _arr(err_dev, "err_dev", 4, 1)
+    cap = _pairs(pairs, _dev(ctx))
+    kd, ed = _arr(k_dev, "k_dev", 8, 1, dev=_dev(ctx)), _arr(err_dev, "err_dev", 4, 1, dev=_dev(ctx))
     _check(lib().ddm_write_async(ctx, upd_begin, upd_end, _ptr(pairs), cap, kd, ed,
                                  _stream(stream)), "ddm_write_async")
 
@@ -310,12 +329,12 @@ def ddm_match_moved(ctx: int, lo, hi, ids, pairs, flags: int = DDM_CLOSED, strea
     """Pairs of k moved extents (d x k device tensors) against the context's
     tree, the moved extents named by ids (uint32/int32 device tensor of k
     entries, or None for 0..k-1); see ddm.h."""
-    d, l, h, k = _set(lo, hi)
+    d, l, h, k = _set(lo, hi, _dev(ctx))
     if ids is not None and ids.shape[0] != k:
         raise ValueError("ids needs one entry per moved extent")
-    cap = _pairs(pairs)
+    cap = _pairs(pairs, _dev(ctx))
     kk = ctypes.c_uint64(0)
-    rc = lib().ddm_match_moved(ctx, l, h, k, _arr(ids, "ids", 4, k), flags, _ptr(pairs), cap,
+    rc = lib().ddm_match_moved(ctx, l, h, k, _arr(ids, "ids", 4, k, dev=_dev(ctx)), flags, _ptr(pairs), cap,
                                ctypes.byref(kk), _stream(stream))
     _check(rc, "ddm_match_moved", kk.value)
     return kk.value
@@ -327,15 +346,15 @@ def ddm_pair_offsets_async(ctx: int, upd_off, pair_off, stream=None) -> None:
     count = upd_off.shape[0] - 1
     if count < 0 or pair_off.shape[0] < count + 1:
         raise ValueError("upd_off and pair_off need count + 1 entries")
-    _check(lib().ddm_pair_offsets_async(ctx, _arr(upd_off, "upd_off", 8, count + 1), count,
-                                        _arr(pair_off, "pair_off", 8, count + 1), _stream(stream)),
+    _check(lib().ddm_pair_offsets_async(ctx, _arr(upd_off, "upd_off", 8, count + 1, dev=_dev(ctx)), count,
+                                        _arr(pair_off, "pair_off", 8, count + 1, dev=_dev(ctx)), _stream(stream)),
            "ddm_pair_offsets_async")
 
 
 def ddm_write(ctx: int, upd_begin: int, upd_end: int, pairs, stream=None) -> int:
     """Write the pairs of the current plan's updates with ids in [upd_begin,
     upd_end), laid out by update id; returns the pair count."""
-    cap = _pairs(pairs)
+    cap = _pairs(pairs, _dev(ctx))
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write(ctx, upd_begin, upd_end, _ptr(pairs), cap, ctypes.byref(k),
                          _stream(stream))
@@ -356,14 +375,14 @@ def ddm_plan_order(ctx: int, order=None, order_offsets=None, stream=None) -> Non
     """The plan's spatial query order: `order` (int32 device tensor, m) gets
     the update at each plan position, `order_offsets` (int64, m + 1) where each
     position's pairs start; either may be None."""
-    o, oo = _arr(order, "order", 4), _arr(order_offsets, "order_offsets", 8)
+    o, oo = _arr(order, "order", 4, dev=_dev(ctx)), _arr(order_offsets, "order_offsets", 8, dev=_dev(ctx))
     _check(lib().ddm_plan_order(ctx, o, oo, _stream(stream)), "ddm_plan_order")
 
 
 def ddm_write_ordered(ctx: int, pos_begin: int, pos_end: int, pairs, stream=None) -> int:
     """Write the pairs of plan positions [pos_begin, pos_end), grouped by
     update in plan order; returns the pair count."""
-    cap = _pairs(pairs)
+    cap = _pairs(pairs, _dev(ctx))
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write_ordered(ctx, pos_begin, pos_end, _ptr(pairs), cap, ctypes.byref(k),
                                  _stream(stream))
@@ -374,7 +393,7 @@ def ddm_write_ordered(ctx: int, pos_begin: int, pos_end: int, pairs, stream=None
 def ddm_write_ordered_ids(ctx: int, pos_begin: int, pos_end: int, sub_ids, stream=None) -> int:
     """Compressed output: the subscription ids of ddm_write_ordered's pairs
     (same positions) into a 1-D int32 tensor; returns the id count."""
-    cap = _ids(sub_ids)
+    cap = _ids(sub_ids, _dev(ctx))
     k = ctypes.c_uint64(0)
     rc = lib().ddm_write_ordered_ids(ctx, pos_begin, pos_end, _ptr(sub_ids), cap,
                                      ctypes.byref(k), _stream(stream))
@@ -405,8 +424,8 @@ def ddm_tree_export(ctx: int, order=None, node_lo=None, node_hi=None, stream=Non
     at each sorted position; `node_lo` / `node_hi` (float32, d * total) each
     node's minlower / maxupper per dimension, entry k * total + j, levels
     stored one after another from level 1.  Any output may be None."""
-    _check(lib().ddm_tree_export(ctx, _arr(order, "order", 4), _arr(node_lo, "node_lo", 4),
-                                 _arr(node_hi, "node_hi", 4),
+    _check(lib().ddm_tree_export(ctx, _arr(order, "order", 4, dev=_dev(ctx)), _arr(node_lo, "node_lo", 4, dev=_dev(ctx)),
+                                 _arr(node_hi, "node_hi", 4, dev=_dev(ctx)),
                                  _stream(stream)), "ddm_tree_export")
 
 
@@ -437,24 +456,36 @@ def ddm_debug_launch_count() -> int:
 
 
 def ddm_scan_counts_noalloc(counts, offsets, stream=None) -> None:
-    """Offsets (int64 device tensor, m + 1) from per-update counts (int32
-    device tensor, m) without any allocation; see include/ddm.h."""
-    _check(lib().ddm_scan_counts_noalloc(_arr(counts, "counts", 4), counts.shape[0],
-                                         _arr(offsets, "offsets", 8, counts.shape[0] + 1),
-                                         _stream(stream)), "ddm_scan_counts_noalloc")
+    """Offsets (int64 device tensor, m + 1) from per-update counts (1-D int32
+    device tensor of m uint32 counts, m <= DDM_NOALLOC_MAX_UPDATES) without
+    any allocation; see include/ddm.h.  Both tensors must be on the current
+    CUDA device, whose stream the work goes to unless `stream` is given."""
+    import torch
+    if counts.dim() != 1 or counts.dtype != torch.int32:
+        raise TypeError("counts must be a 1-D int32 tensor (uint32 counts)")
+    m = counts.shape[0]
+    if m > DDM_NOALLOC_MAX_UPDATES:  # also keeps m inside the uint32 argument
+        raise ValueError(f"{m} counts; the allocation-free scan takes at most "
+                         f"{DDM_NOALLOC_MAX_UPDATES}")
+    if offsets.dim() != 1 or offsets.dtype != torch.int64:
+        raise TypeError("offsets must be a 1-D int64 tensor")
+    dev = torch.cuda.current_device()
+    c = _arr(counts, "counts", 4, dev=dev)
+    o = _arr(offsets, "offsets", 8, m + 1, dev=dev)
+    _check(lib().ddm_scan_counts_noalloc(c, m, o, _stream(stream)), "ddm_scan_counts_noalloc")
 
 
 def ddm_batch_match(ctx: int, upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub_off, pairs,
                     pair_off=None, flags: int = DDM_CLOSED, stream=None) -> int:
     """Batched instances (see include/ddm.h).  upd_off / sub_off: int64 device
     tensors of count + 1 offsets; pairs: int32 device tensor (capacity, 2)."""
-    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi, _dev(ctx))
     count = upd_off.shape[0] - 1
-    cap = _pairs(pairs)
+    cap = _pairs(pairs, _dev(ctx))
     k = ctypes.c_uint64(0)
-    uo = _arr(upd_off, "upd_off", 8, count + 1)
-    so = _arr(sub_off, "sub_off", 8, count + 1)
-    po = _arr(pair_off, "pair_off", 8, count + 1)
+    uo = _arr(upd_off, "upd_off", 8, count + 1, dev=_dev(ctx))
+    so = _arr(sub_off, "sub_off", 8, count + 1, dev=_dev(ctx))
+    po = _arr(pair_off, "pair_off", 8, count + 1, dev=_dev(ctx))
     rc = lib().ddm_batch_match(ctx, d, count, ul, uh, uo, m, sl, sh, so, n, flags, _ptr(pairs), cap,
                                po, ctypes.byref(k), _stream(stream))
     _check(rc, "ddm_batch_match", k.value)
@@ -465,13 +496,13 @@ def ddm_batch_match_async(ctx: int, upd_lo, upd_hi, upd_off, sub_lo, sub_hi, sub
                           pair_off=None, k_dev=None, err_dev=None, flags: int = DDM_CLOSED,
                           stream=None) -> None:
     """Host-synchronisation-free batched match (capturable in a CUDA graph)."""
-    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi)
+    d, ul, uh, m, sl, sh, n = _two_sets(upd_lo, upd_hi, sub_lo, sub_hi, _dev(ctx))
     count = upd_off.shape[0] - 1
-    cap = _pairs(pairs)
-    uo = _arr(upd_off, "upd_off", 8, count + 1)
-    so = _arr(sub_off, "sub_off", 8, count + 1)
-    po = _arr(pair_off, "pair_off", 8, count + 1)
+    cap = _pairs(pairs, _dev(ctx))
+    uo = _arr(upd_off, "upd_off", 8, count + 1, dev=_dev(ctx))
+    so = _arr(sub_off, "sub_off", 8, count + 1, dev=_dev(ctx))
+    po = _arr(pair_off, "pair_off", 8, count + 1, dev=_dev(ctx))
     rc = lib().ddm_batch_match_async(ctx, d, count, ul, uh, uo, m, sl, sh, so, n, flags,
-                                     _ptr(pairs), cap, po, _arr(k_dev, "k_dev", 8, 1),
-                                     _arr(err_dev, "err_dev", 4, 1), _stream(stream))
+                                     _ptr(pairs), cap, po, _arr(k_dev, "k_dev", 8, 1, dev=_dev(ctx)),
+                                     _arr(err_dev, "err_dev", 4, 1, dev=_dev(ctx)), _stream(stream))
     _check(rc, "ddm_batch_match_async")

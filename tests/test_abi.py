@@ -129,3 +129,95 @@ def test_binding_rejects_host_and_mistyped_arrays():
         ddm.ddm_write_ordered_ids(0, 0, 1, torch.zeros(4, dtype=torch.int64))       # int64
     with pytest.raises(ValueError):
         ddm.ddm_write_ordered_ids(0, 0, 1, torch.zeros(4, dtype=torch.int32))       # host
+
+
+class _FakeCuda:
+    """Stands in for a CUDA tensor on `index` (no GPU needed): the binding's
+    checks only read these attributes, and every check below fails before
+    any pointer reaches the library."""
+
+    def __init__(self, shape, dtype, index):
+        import torch
+        self.shape = torch.Size(shape)
+        self.dtype = dtype
+        self.is_cuda = True
+        self.device = torch.device("cuda", index)
+
+    def dim(self):
+        return len(self.shape)
+
+    def numel(self):
+        n = 1
+        for s in self.shape:
+            n *= s
+        return n
+
+    def element_size(self):
+        import torch
+        return torch.empty(0, dtype=self.dtype).element_size()
+
+    def is_contiguous(self):
+        return True
+
+    def data_ptr(self):
+        return 0
+
+
+class _NoLibrary:
+    """Takes the library's place: any call into it fails the test."""
+
+    def __getattr__(self, name):
+        raise AssertionError(f"{name} was called although a check should have failed")
+
+
+def test_binding_rejects_tensors_on_another_device(monkeypatch):
+    """A context lives on one GPU; its kernels would dereference a peer GPU's
+    pointer.  The binding records each context's device and refuses tensors
+    on any other one before calling the library (no GPU needed: fake handles
+    and tensors)."""
+    import torch
+    fake_ctx = 0x5151
+    monkeypatch.setitem(ddm._CTX_DEVICE, fake_ctx, 0)
+    monkeypatch.setattr(ddm, "_lib", _NoLibrary())
+    f32 = torch.float32
+    on0 = _FakeCuda((2, 8), f32, 0)
+    on1 = _FakeCuda((2, 8), f32, 1)
+    with pytest.raises(ValueError, match="cuda:1"):
+        ddm.ddm_count(fake_ctx, on1, on1, on1, on1)
+    with pytest.raises(ValueError, match="cuda:1"):
+        ddm.ddm_build(fake_ctx, on1, on1)
+    with pytest.raises(ValueError, match="cuda:1"):
+        ddm.ddm_plan(fake_ctx, on1, on1)
+    with pytest.raises(ValueError, match="cuda:1"):  # sets fine, pair buffer elsewhere
+        ddm.ddm_match(fake_ctx, on0, on0, on0, on0, _FakeCuda((16, 2), torch.int32, 1))
+    with pytest.raises(ValueError, match="cuda:1"):
+        ddm.ddm_write_ordered_ids(fake_ctx, 0, 1, _FakeCuda((16,), torch.int32, 1))
+    with pytest.raises(ValueError, match="cuda:1"):
+        ddm.ddm_plan_order(fake_ctx, _FakeCuda((8,), torch.int32, 1))
+    # the allocation-free scan runs on the current device
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    with pytest.raises(ValueError, match="cuda:1"):
+        ddm.ddm_scan_counts_noalloc(_FakeCuda((8,), torch.int32, 1),
+                                    _FakeCuda((9,), torch.int64, 0))
+
+
+def test_binding_rejects_counts_the_c_abi_cannot_carry(monkeypatch):
+    """Sizes go to uint32 arguments: the binding refuses what would be
+    truncated, and mistyped counts, before any library call."""
+    import torch
+    monkeypatch.setattr(ddm, "_lib", _NoLibrary())
+    big = _FakeCuda((ddm.DDM_NOALLOC_MAX_UPDATES + 1,), torch.int32, 0)
+    off = _FakeCuda((ddm.DDM_NOALLOC_MAX_UPDATES + 2,), torch.int64, 0)
+    with pytest.raises(ValueError, match="at most"):
+        ddm.ddm_scan_counts_noalloc(big, off)
+    with pytest.raises(ValueError, match="at most"):
+        ddm.ddm_scan_counts_noalloc(_FakeCuda(((1 << 32) + 3,), torch.int32, 0), off)
+    with pytest.raises(TypeError):
+        ddm.ddm_scan_counts_noalloc(_FakeCuda((8,), torch.float32, 0),
+                                    _FakeCuda((9,), torch.int64, 0))
+    with pytest.raises(TypeError):
+        ddm.ddm_scan_counts_noalloc(_FakeCuda((8,), torch.int32, 0),
+                                    _FakeCuda((9,), torch.int32, 0))
+    huge = _FakeCuda((1, ddm.DDM_MAX_EXTENTS + 1), torch.float32, 0)
+    with pytest.raises(ValueError, match="at most"):
+        ddm.ddm_build(0x5151, huge, huge)
