@@ -405,10 +405,9 @@ int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);
 /* ---------------------------------------------------------------------- */
 
 /* The paper has no counterpart to this call; it serves callers that cannot
- * allocate device memory when they need it: code recording a stream into a
- * CUDA graph (cudaMalloc cannot be captured), real-time loops that must not
- * block in the allocator, hosts whose device memory all belongs to another
- * allocator.
+ * allocate device memory when they need it: real-time loops that must not
+ * block in the allocator (cudaMalloc and cudaFree can synchronise the whole
+ * device), and hosts whose device memory all belongs to another allocator.
  *
  * Exclusive prefix sum of per-update match counts: offsets[j] =
  * counts[0] + ... + counts[j-1] for j <= m, so update j's pairs are
@@ -416,13 +415,16 @@ int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);
  * offsets[m] = K -- the same result as the offsets of ddm_plan for the same
  * counts.  counts (m uint32) and offsets (m + 1 uint64) are DEVICE pointers
  * of the current device, owned by the caller; work is enqueued on `stream`
- * and nothing is synchronised or allocated.  Scratch is a fixed device
- * array inside the library, so m must not exceed DDM_NOALLOC_MAX_UPDATES
- * (DDM_ERR_ARG otherwise; also for NULL pointers).  The array is shared by
- * every call on a device: calls whose work may overlap on the GPU race and
- * must be serialised by the caller.  The first call on a device looks up
- * the array's device address (DDM_ERR_CUDA if that fails); make that first
- * call before any stream capture. */
+ * and nothing is synchronised or allocated.  offsets must not be NULL;
+ * counts may be NULL only when m == 0 (offsets[0] = 0 is then written).
+ * Scratch is a fixed device array inside the library, so m must not exceed
+ * DDM_NOALLOC_MAX_UPDATES (DDM_ERR_ARG otherwise, and for a NULL pointer the
+ * call needs).  The array is shared by every call on a device and keeps the
+ * last call's tile sums; every call rewrites the sums it reads, so nothing
+ * needs clearing, but calls whose work may overlap on the GPU race and must
+ * be serialised by the caller.  The first call on a device looks up the
+ * array's device address (DDM_ERR_CUDA if that fails); make that first call
+ * before any stream capture. */
 #define DDM_NOALLOC_MAX_UPDATES 67108864u  /* 2^26 updates: 128 KiB of scratch */
 int ddm_scan_counts_noalloc(const uint32_t *counts, uint32_t m, uint64_t *offsets,
                             void *stream);

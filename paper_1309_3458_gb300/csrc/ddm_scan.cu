@@ -6,6 +6,8 @@
 // reduce-then-scan over tiles of 4096 counts: per-tile sums, one CTA scans
 // the tile sums, then each tile scans its counts from its tile offset.  No
 // kernel waits on another CTA.
+#include <atomic>
+
 #include "ddm_internal.cuh"
 
 namespace ddm {
@@ -196,11 +198,11 @@ cudaError_t launch_chunk_end(const unsigned long long* offsets, uint32_t m, uint
 // Allocation-free variant of the offsets scan (ddm_scan_counts_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need the
-// offsets: a stream being captured into a CUDA graph (cudaMalloc cannot be
-// captured), a real-time loop that must not block in the allocator, or a
-// host that hands all device memory to its own pool.  This entry point runs
-// the same three scan kernels as launch_scan, with the per-tile sums kept in
-// a fixed device array instead of a context buffer.
+// offsets: a real-time loop that must not block in the allocator (cudaMalloc
+// and cudaFree can synchronise the whole device), or a host that hands all
+// device memory to its own pool.  This entry point runs the same three scan
+// kernels as launch_scan, with the per-tile sums kept in a fixed device array
+// instead of a context buffer.
 //
 // Limits and sharing: the array holds kNoallocTiles tile sums, so m may be
 // at most DDM_NOALLOC_MAX_UPDATES (= kNoallocTiles * 4096); every GPU that
@@ -218,9 +220,11 @@ static __device__ __align__(256) unsigned long long g_noalloc_tile_sums[kNoalloc
 namespace {
 
 // Device address of g_noalloc_tile_sums per device, looked up once per device
-// (host code cannot use the symbol itself as a device pointer).
+// (host code cannot use the symbol itself as a device pointer).  Two host
+// threads that make their first call on a device at the same time both look
+// the address up and store the same value; the atomics make that race benign.
 constexpr int kMaxDevices = 64;
-unsigned long long* g_noalloc_ptr[kMaxDevices] = {};
+std::atomic<unsigned long long*> g_noalloc_ptr[kMaxDevices];
 
 }  // namespace
 
@@ -236,17 +240,18 @@ extern "C" int ddm_scan_counts_noalloc(const uint32_t* counts, uint32_t m, uint6
     cudaGetLastError();
     return DDM_ERR_CUDA;
   }
-  if (!g_noalloc_ptr[dev]) {
+  unsigned long long* sums = g_noalloc_ptr[dev].load(std::memory_order_acquire);
+  if (!sums) {
     void* p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_tile_sums) != cudaSuccess || !p) {
       cudaGetLastError();
       return DDM_ERR_CUDA;
     }
-    g_noalloc_ptr[dev] = static_cast<unsigned long long*>(p);
+    sums = static_cast<unsigned long long*>(p);
+    g_noalloc_ptr[dev].store(sums, std::memory_order_release);
   }
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const uint32_t tiles = (m + kScanTile - 1) / kScanTile;
-  unsigned long long* sums = g_noalloc_ptr[dev];
   auto* off = reinterpret_cast<unsigned long long*>(offsets);
   if (tiles > 0) k_tile_sums<<<tiles, kThreads, 0, s>>>(counts, m, sums);
   k_scan_sums<<<1, kThreads, 0, s>>>(sums, tiles, off, m, nullptr);
