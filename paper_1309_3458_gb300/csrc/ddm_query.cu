@@ -29,8 +29,11 @@
 // the same order -- either way the pairs come out exactly as counted, in
 // tree order.  The write pass can also store only each pair's subscription
 // id (the compressed form of the intersection matrix, Section III), or the
-// pairs with their fields exchanged when the roles are swapped.  Predicates
-// are combined with bitwise ANDs so the per-query test has no branches.
+// pairs with their fields exchanged when the roles are swapped.  For d <= 3
+// the count pass's leaf tests are hand-written PTX: the 2d segment
+// comparisons chain one predicate (setp with .and) into a vote or a
+// predicated or, with no branch and no integer form of the predicate; other
+// paths combine the comparisons with bitwise ANDs, also without branches.
 #include <cfloat>
 #include <type_traits>
 
@@ -75,6 +78,90 @@ __device__ __forceinline__ float warp_min(float v) {
   return v;
 }
 
+// Ballot of the d-dimensional segment test (Alg. 1 in every dimension,
+// Section III-A) of this lane's subscription e against one query, for
+// d = 1..3: one predicate chained through 2d compare-and-accumulate setp
+// instructions and one vote, with no integer form of the predicate.  b0 / b1
+// hold the query's (lo, hi) pairs of dimensions (0, 1) and 2.  A padding lane
+// carries NaN bounds, which fail every comparison.
+#define DDM_SEG_BALLOT(CMP)                                                              \
+  template <int D>                                                                        \
+  __device__ __forceinline__ uint32_t seg_ballot_##CMP(const float2* e, float4 b0, float4 b1) { \
+    uint32_t hb;                                                                          \
+    if (D == 1) {                                                                         \
+      asm("{\n\t.reg .pred p;\n\t"                                                       \
+          "setp." #CMP ".f32 p, %1, %2;\n\t"                                              \
+          "setp." #CMP ".and.f32 p, %3, %4, p;\n\t"                                       \
+          "vote.sync.ballot.b32 %0, p, 0xffffffff;\n\t}"                                  \
+          : "=r"(hb) : "f"(e[0].x), "f"(b0.y), "f"(b0.x), "f"(e[0].y));                   \
+    } else if (D == 2) {                                                                  \
+      asm("{\n\t.reg .pred p;\n\t"                                                       \
+          "setp." #CMP ".f32 p, %1, %2;\n\t"                                              \
+          "setp." #CMP ".and.f32 p, %3, %4, p;\n\t"                                       \
+          "setp." #CMP ".and.f32 p, %5, %6, p;\n\t"                                       \
+          "setp." #CMP ".and.f32 p, %7, %8, p;\n\t"                                       \
+          "vote.sync.ballot.b32 %0, p, 0xffffffff;\n\t}"                                  \
+          : "=r"(hb) : "f"(e[0].x), "f"(b0.y), "f"(b0.x), "f"(e[0].y),                    \
+            "f"(e[1].x), "f"(b0.w), "f"(b0.z), "f"(e[1].y));                               \
+    } else {                                                                              \
+      asm("{\n\t.reg .pred p;\n\t"                                                       \
+          "setp." #CMP ".f32 p, %1, %2;\n\t"                                              \
+          "setp." #CMP ".and.f32 p, %3, %4, p;\n\t"                                       \
+          "setp." #CMP ".and.f32 p, %5, %6, p;\n\t"                                       \
+          "setp." #CMP ".and.f32 p, %7, %8, p;\n\t"                                       \
+          "setp." #CMP ".and.f32 p, %9, %10, p;\n\t"                                      \
+          "setp." #CMP ".and.f32 p, %11, %12, p;\n\t"                                     \
+          "vote.sync.ballot.b32 %0, p, 0xffffffff;\n\t}"                                  \
+          : "=r"(hb) : "f"(e[0].x), "f"(b0.y), "f"(b0.x), "f"(e[0].y),                    \
+            "f"(e[1].x), "f"(b0.w), "f"(b0.z), "f"(e[1].y),                               \
+            "f"(e[2].x), "f"(b1.y), "f"(b1.x), "f"(e[2].y));                               \
+    }                                                                                     \
+    return hb;                                                                            \
+  }
+DDM_SEG_BALLOT(le)  // closed segments
+DDM_SEG_BALLOT(lt)  // the strict test of Alg. 1
+#undef DDM_SEG_BALLOT
+
+// The same test with the roles swapped (lane = query, one subscription b of
+// the leaf broadcast from shared memory, for d = 1..3): `bit` is or-ed into
+// acc when the lane's query [ql, qh] meets b in every dimension.
+#define DDM_SEG_OR(CMP)                                                                    \
+  template <int D>                                                                          \
+  __device__ __forceinline__ void seg_or_##CMP(uint32_t& acc, uint32_t bit, float4 b0,      \
+                                               float4 b1, const float* ql, const float* qh) { \
+    if (D == 1) {                                                                           \
+      asm("{\n\t.reg .pred p;\n\t"                                                         \
+          "setp." #CMP ".f32 p, %2, %3;\n\t"                                                \
+          "setp." #CMP ".and.f32 p, %4, %5, p;\n\t"                                         \
+          "@p or.b32 %0, %0, %1;\n\t}"                                                      \
+          : "+r"(acc) : "r"(bit), "f"(b0.x), "f"(qh[0]), "f"(ql[0]), "f"(b0.y));            \
+    } else if (D == 2) {                                                                    \
+      asm("{\n\t.reg .pred p;\n\t"                                                         \
+          "setp." #CMP ".f32 p, %2, %3;\n\t"                                                \
+          "setp." #CMP ".and.f32 p, %4, %5, p;\n\t"                                         \
+          "setp." #CMP ".and.f32 p, %6, %7, p;\n\t"                                         \
+          "setp." #CMP ".and.f32 p, %8, %9, p;\n\t"                                         \
+          "@p or.b32 %0, %0, %1;\n\t}"                                                      \
+          : "+r"(acc) : "r"(bit), "f"(b0.x), "f"(qh[0]), "f"(ql[0]), "f"(b0.y),             \
+            "f"(b0.z), "f"(qh[1]), "f"(ql[1]), "f"(b0.w));                                  \
+    } else {                                                                                \
+      asm("{\n\t.reg .pred p;\n\t"                                                         \
+          "setp." #CMP ".f32 p, %2, %3;\n\t"                                                \
+          "setp." #CMP ".and.f32 p, %4, %5, p;\n\t"                                         \
+          "setp." #CMP ".and.f32 p, %6, %7, p;\n\t"                                         \
+          "setp." #CMP ".and.f32 p, %8, %9, p;\n\t"                                         \
+          "setp." #CMP ".and.f32 p, %10, %11, p;\n\t"                                       \
+          "setp." #CMP ".and.f32 p, %12, %13, p;\n\t"                                       \
+          "@p or.b32 %0, %0, %1;\n\t}"                                                      \
+          : "+r"(acc) : "r"(bit), "f"(b0.x), "f"(qh[0]), "f"(ql[0]), "f"(b0.y),             \
+            "f"(b0.z), "f"(qh[1]), "f"(ql[1]), "f"(b0.w),                                    \
+            "f"(b1.x), "f"(qh[2]), "f"(ql[2]), "f"(b1.y));                                   \
+    }                                                                                       \
+  }
+DDM_SEG_OR(le)
+DDM_SEG_OR(lt)
+#undef DDM_SEG_OR
+
 // D > 0: compile-time dimension count; D == 0: runtime d (up to 8).
 // BATCH: every query matches only its instance's subscription positions, and
 // pairs carry instance-local ids.
@@ -85,8 +172,14 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
           uint32_t* __restrict__ work, Status* __restrict__ st) {
   constexpr int DM = D > 0 ? D : DDM_MAX_DIMS;
   constexpr int DP = (DM + 1) / 2;  // dimension pairs: one 128-bit shared load each
+  // Per query a row of RW float4: its bounds, dimension pairs first, and one
+  // word for its hit mask in the leaf being tested (in the unused half of the
+  // last pair for odd DM, else in a float4 of its own).
+  constexpr int RW = (DM & 1) ? DP : DP + 1;
+  constexpr int HB = (DM & 1) ? 4 * (DP - 1) + 2 : 4 * DP;  // hit-mask word within a row
   const int d = D > 0 ? D : t.d;
-  __shared__ float4 s_q[kWarps][32][DP];
+  __shared__ float4 s_q[kWarps][32][RW];
+  __shared__ uint32_t s_list[WRITE ? 1 : kWarps][32];  // count pass: rows of a leaf's queries
   __shared__ float4 s_e[WRITE ? 1 : kWarps][32][DP];  // count pass: a leaf's subscriptions
   __shared__ uint2 s_rng[kWarps][BATCH ? 32 : 1];  // per query: its instance's positions
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
@@ -204,7 +297,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
         float2 ev[DM];
 #pragma unroll
         for (int k = 0; k < DM; ++k)
-          if (k < d) ev[k] = iv ? t.e[k * n + i] : make_float2(INFINITY, -INFINITY);
+          if (k < d) ev[k] = iv ? t.e[k * n + i] : make_float2(NAN, NAN);  // fails every test
         uint32_t my_sid = 0;
         if (WRITE && iv) my_sid = t.sid[i];
         uint32_t my_hb = 0;  // count pass: this lane's query's hit mask in the leaf
@@ -221,19 +314,30 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
           }
           __syncwarp();
           uint32_t hbm = 0;
-#pragma unroll 8
-          for (int e = 0; e < 32; ++e) {
-            bool hit = true;
+          if constexpr (D >= 1 && D <= 3) {
 #pragma unroll
-            for (int k2 = 0; k2 < DP; ++k2) {
-              if (2 * k2 < d) {
-                const float4 b = s_e[wib][e][k2];
-                hit = hit & le<OPEN>(b.x, qh[2 * k2]) & le<OPEN>(ql[2 * k2], b.y);
-                if (2 * k2 + 1 < d)
-                  hit = hit & le<OPEN>(b.z, qh[2 * k2 + 1]) & le<OPEN>(ql[2 * k2 + 1], b.w);
-              }
+            for (int e = 0; e < 32; ++e) {
+              const float4 b0 = s_e[wib][e][0], b1 = D == 3 ? s_e[wib][e][DP - 1] : b0;
+              if (OPEN)
+                seg_or_lt<D>(hbm, 1u << e, b0, b1, ql, qh);
+              else
+                seg_or_le<D>(hbm, 1u << e, b0, b1, ql, qh);
             }
-            hbm |= (hit ? 1u : 0u) << e;
+          } else {  // runtime d (up to 8)
+#pragma unroll 8
+            for (int e = 0; e < 32; ++e) {
+              bool hit = true;
+#pragma unroll
+              for (int k2 = 0; k2 < DP; ++k2) {
+                if (2 * k2 < d) {
+                  const float4 b = s_e[wib][e][k2];
+                  hit = hit & le<OPEN>(b.x, qh[2 * k2]) & le<OPEN>(ql[2 * k2], b.y);
+                  if (2 * k2 + 1 < d)
+                    hit = hit & le<OPEN>(b.z, qh[2 * k2 + 1]) & le<OPEN>(ql[2 * k2 + 1], b.w);
+                }
+              }
+              hbm |= (hit ? 1u : 0u) << e;
+            }
           }
           __syncwarp();
           hbm &= __ballot_sync(0xffffffffu, iv);  // padding lanes of the last leaf
@@ -246,6 +350,50 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
             hbm &= upto_b & ~upto_a;
           }
           my_hb = ((qm >> lane) & 1u) ? hbm : 0u;
+          qm = 0u;
+        }
+        if (!WRITE && qm) {
+          // Queries of the leaf as a list of row offsets (in float4 units);
+          // two per iteration, each the segment tests of Alg. 1 in every
+          // dimension and one ballot, its hit mask stored into its row (every
+          // lane stores the same word).
+          const bool mine = (qm >> lane) & 1u;
+          const uint32_t nq = __popc(qm);
+          if (mine) s_list[wib][__popc(qm & lt)] = (uint32_t)(lane * RW);
+          __syncwarp();
+          const float4* rows = &s_q[wib][0][0];
+          uint32_t* hbw = reinterpret_cast<uint32_t*>(&s_q[wib][0][0]);
+          auto test = [&](uint32_t r) {
+            if constexpr (D >= 1 && D <= 3 && !BATCH) {
+              const float4 b0 = rows[r], b1 = D == 3 ? rows[r + 1] : b0;
+              hbw[4 * r + HB] = OPEN ? seg_ballot_lt<D>(ev, b0, b1) : seg_ballot_le<D>(ev, b0, b1);
+              return;
+            }
+            bool hit = iv;
+            if (BATCH) {
+              const uint2 rg = s_rng[wib][r / RW];
+              hit = hit & (i >= rg.x) & (i < rg.y);
+            }
+#pragma unroll
+            for (int k2 = 0; k2 < DP; ++k2) {
+              if (2 * k2 < d) {
+                const float4 b = rows[r + k2];
+                hit = hit & le<OPEN>(ev[2 * k2].x, b.y) & le<OPEN>(b.x, ev[2 * k2].y);
+                if (2 * k2 + 1 < d)
+                  hit = hit & le<OPEN>(ev[2 * k2 + 1].x, b.w) & le<OPEN>(b.z, ev[2 * k2 + 1].y);
+              }
+            }
+            hbw[4 * r + HB] = __ballot_sync(0xffffffffu, hit);
+          };
+          uint32_t j = 0;
+          for (; j + 2u <= nq; j += 2u) {
+            const uint2 rr = *reinterpret_cast<const uint2*>(&s_list[wib][j]);
+            test(rr.x);
+            test(rr.y);
+          }
+          if (j < nq) test(s_list[wib][j]);
+          __syncwarp();
+          my_hb = mine ? hbw[4 * lane * RW + HB] : 0u;
           qm = 0u;
         }
         while (qm) {
