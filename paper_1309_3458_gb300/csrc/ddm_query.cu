@@ -613,8 +613,9 @@ __device__ __forceinline__ void st_hinted(uint32_t* a, uint32_t v, unsigned long
 // by one broadcast from shared memory: the lanes whose bit is set in the hit
 // mask load their subscription ids (one 128-byte load for the whole leaf) and
 // store their pairs at the record's position plus their rank among the set
-// bits -- one contiguous run of the output per record.  Eight records are in
-// flight at a time (their id loads issued before their stores).  Positions
+// bits -- one contiguous run of the output per record.  A group of records
+// (ReplayShape) is in flight at a time (their id loads issued before their
+// stores).  Positions
 // are relative to the range's first pair; with fewer than 2^32 pairs in the
 // range (WIDE false) they are 32-bit.  OUT fixes the output form at compile
 // time: kOutPairs {update, subscription}; kOutSwapped the same with the
@@ -622,8 +623,21 @@ __device__ __forceinline__ void st_hinted(uint32_t* a, uint32_t v, unsigned long
 // compressed output, only each pair's subscription id (4 bytes) at the
 // pair's position.
 constexpr int kOutPairs = 0, kOutSwapped = 1, kOutIds = 2;
+// Resident CTAs per SM and records expanded per group (their id loads issued
+// before their stores) of the replay kernel, by output form.  Pairs (8-byte
+// stores): two CTAs of eight warps with sixteen records in flight each (128
+// registers, no spill) beat four CTAs with eight (64 registers, spilling):
+// 131.9 against 147.4 ms per step on the clustered d = 3 workload; one CTA,
+// or four records per group, was slower.  Subscription ids (4-byte stores)
+// go the other way: four CTAs with eight records take 122.3 ms, three 138.0,
+// two 178.7.
+template <int OUT>
+struct ReplayShape {
+  static constexpr int ctas = OUT == 2 ? 4 : 2;
+  static constexpr int group = OUT == 2 ? 8 : 16;
+};
 template <bool FILTER_ID, bool WIDE, bool BATCH, int OUT>
-__global__ void __launch_bounds__(kThreads, 4)
+__global__ void __launch_bounds__(kThreads, ReplayShape<OUT>::ctas)
 k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uint32_t p0,
          uint32_t p1, uint32_t pb, uint32_t pe, uint32_t idb, uint32_t ide,
          uint32_t* __restrict__ work, Status* __restrict__ st) {
@@ -704,17 +718,18 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
       if (!kPacked) s_at[wib][lane] = o;
       __syncwarp();
 #pragma unroll 1
-      for (int g = 0; g < 32; g += 8) {
-        uint4 rr[8];
-        uint32_t sv[8];
+      constexpr int G = ReplayShape<OUT>::group;
+      for (int g = 0; g < 32; g += G) {
+        uint4 rr[G];
+        uint32_t sv[G];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < G; ++u) {
           rr[u] = s_rec[wib][g + u];
           sv[u] = 0u;
           if (rr[u].y & lanebit) sv[u] = ld_hinted(sid + rr[u].x * 32u + (uint32_t)lane, keep);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < G; ++u) {
           if (rr[u].y & lanebit) {
             const Cursor at = kPacked ? (Cursor)rr[u].w : s_at[wib][g + u];
             const unsigned long long slot = (unsigned long long)(at + (Cursor)__popc(rr[u].y & below));
@@ -775,12 +790,12 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, const BatchVie
 }
 
 template <bool FILTER_ID, bool BATCH>
-void dispatch_replay(bool wide, uint32_t blocks, cudaStream_t s, const TreeView& t,
+void dispatch_replay(bool wide, uint32_t sms, cudaStream_t s, const TreeView& t,
                      const QueryView& q, const BatchView& bv, const RecordArena& ra,
                      const WriteView& w, uint32_t p0, uint32_t p1, uint32_t pb, uint32_t pe,
                      uint32_t idb, uint32_t ide, uint32_t* work, Status* st) {
 #define DDM_REPLAY(F, WD, OUT)                                                              \
-  k_replay<F, WD, BATCH, OUT><<<blocks, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe, idb, \
+  k_replay<F, WD, BATCH, OUT><<<sms * ReplayShape<OUT>::ctas, kThreads, 0, s>>>(t, q, bv, ra, w, p0, p1, pb, pe, idb, \
                                                           ide, work, st)
   // Compressed output and swapped roles: whole single problems only (checked
   // by launch_replay), so those forms exist for that case alone.
@@ -840,19 +855,18 @@ cudaError_t launch_replay(const TreeView& t, const QueryView& q, const BatchView
   if ((w.ids || w.swap) && (id_filter || bv.count)) return cudaErrorInvalidValue;  // see dispatch_replay
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
-  const uint32_t blocks = (uint32_t)sms * 4u;  // persistent: work = record blocks
   // Cursors fit 32 bits when the range's pairs do; the capacity bounds them.
   const bool wide = w.capacity > 0xffffffffull;
   if (id_filter) {
     if (bv.count)
-      dispatch_replay<true, true>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+      dispatch_replay<true, true>(wide, (uint32_t)sms, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
     else
-      dispatch_replay<true, false>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+      dispatch_replay<true, false>(wide, (uint32_t)sms, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
   } else {
     if (bv.count)
-      dispatch_replay<false, true>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+      dispatch_replay<false, true>(wide, (uint32_t)sms, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
     else
-      dispatch_replay<false, false>(wide, blocks, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
+      dispatch_replay<false, false>(wide, (uint32_t)sms, s, t, q, bv, ra, w, p0, p1, pb, pe, idb, ide, work, st);
   }
   note_launches(1);
   return cudaGetLastError();
