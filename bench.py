@@ -41,7 +41,8 @@ DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
 # DRAM bytes (read + write) per pair of the write-pass kernel (k_replay), from
 # the ncu capture summarised in profiles/k_replay_clustered_d3_scale0.15.md
 # (a smaller case of the same workload; traffic scales with pairs written).
-TRAFFIC_PER_PAIR = 9.83
+# None until a capture of the current kernel exists.
+TRAFFIC_PER_PAIR = None
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -430,13 +431,20 @@ def serving_section(seconds: float = 2.0, slots: int = 4, saturated_seconds: flo
     return out
 
 
-# ALU pipe of one GB300: 152 SMs x 64 lanes (16 per sub-partition; ncu's
-# own ALU-pipe peak, 0.5 warp instructions per cycle per sub-partition) at
-# the 2,070 MHz maximum SM clock; a float compare is one lane operation.
-ALU_PEAK_GCMP = 152 * 64 * 2.070
+# ALU pipe of one SM: 64 lanes (16 per sub-partition; ncu's own ALU-pipe
+# peak, 0.5 warp instructions per cycle per sub-partition); a float compare is
+# one lane operation.  The peak multiplies this by the device's SM count and
+# the median SM clock sampled during the timed region (the 2,070 MHz maximum
+# when no sample exists).
+ALU_LANES_PER_SM = 64
+MAX_SM_MHZ = 2070.0
 
 
-def count_roofline(leaf_tests, d, count_ms, steps):
+def alu_peak_gcmp(sms, sm_mhz):
+    return sms * ALU_LANES_PER_SM * (sm_mhz or MAX_SM_MHZ) / 1e3
+
+
+def count_roofline(leaf_tests, d, count_ms, steps, sms, sm_mhz):
     """The count pass (`k_packets`, issue / ALU bound): segment comparisons
     the tree walk makes -- 2d per tested subscription, 32 subscriptions per
     (query, leaf) test, counted by the kernel itself -- per second of
@@ -445,10 +453,21 @@ def count_roofline(leaf_tests, d, count_ms, steps):
     sec = sum(a.elapsed_time(b) for a, b in count_ms) / 1e3 / max(1, steps)
     cmp = float(leaf_tests) * 32 * 2 * d
     achieved = cmp / sec / 1e9 if sec > 0 else 0.0
+    peak = alu_peak_gcmp(sms, sm_mhz)
     return {"bound": "alu", "kernel": "k_packets (count pass, ddm_plan)", "achieved": achieved,
-            "peak": ALU_PEAK_GCMP, "unit": "Gcmp/s", "frac": achieved / ALU_PEAK_GCMP,
+            "peak": peak, "unit": "Gcmp/s", "frac": achieved / peak,
             "leaf_tests": int(leaf_tests), "plan_ms_per_step": 1e3 * sec,
-            "peak_source": "unit counts x max SM clock"}
+            "peak_source": f"{sms} SMs x {ALU_LANES_PER_SM} ALU lanes x "
+                           f"{sm_mhz or MAX_SM_MHZ:.0f} MHz ("
+                           + ("median sampled SM clock)" if sm_mhz else "maximum SM clock)")}
+
+
+def query_bytes(d, n, m, K):
+    """Algorithmic bytes of one whole match: every input extent read once
+    (8 d bytes: lower and upper bound per dimension), every pair written once
+    (8 bytes), and the tree build (three passes of 12 bytes per subscription:
+    key, id and bound)."""
+    return {"inputs": 8 * d * (n + m), "pairs": 8 * K, "build": 36 * n}
 
 
 def configs_section(skip: str, reps: int = 3):
@@ -642,7 +661,7 @@ def main():
             if record:
                 s1.record(stream)
                 write_ms.append((s0, s1))
-                write_bytes.append(8 * d * (e - b) + 8 * d * n + 8 * k)
+                write_bytes.append(8 * k)
                 write_pairs.append(k)
             b = e
         return K
@@ -704,7 +723,7 @@ def main():
                 if record:
                     s1.record(stream)
                     cw_ms.append((s0, s1))
-                    cw_bytes.append(8 * d * (e - b) + 8 * d * n + 4 * k)
+                    cw_bytes.append(4 * k)
                     cw_ids.append(k)
                 b = e
             return Kc
@@ -734,7 +753,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "k_replay (ddm_write_ordered_ids)",
                          "achieved": c_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": c_gbs / hbm_peak, "peak_source": peak_src,
-                         "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 4*(ids in chunk)"}}
+                         "bytes_per_launch": "4*(ids in chunk): each id written once"}}
 
     # ---- end to end with host buffers ----
     # Inputs are copied from pinned host memory every step and every pair is
@@ -863,6 +882,12 @@ def main():
         cpu["small_configs"] = cpu_small_configs()
 
     clocks = clk.summary()
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    qb = query_bytes(d, n, m, K)
+    qbytes = qb["inputs"] + qb["pairs"]
+    sbytes = qbytes + qb["build"]
+    q_s = (sum(a.elapsed_time(b) for a, b in count_ms) / 1e3 + write_s) / args.steps
+    step_s = total_ms / 1e3 / args.steps
     line = {
         "metric": METRIC,
         "value": pairs_job / t_job,
@@ -887,15 +912,28 @@ def main():
         "roofline": {"bound": "hbm", "kernel": "k_replay (ddm_write_ordered)",
                      "achieved": write_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": write_gbs / hbm_peak,
-                     "traffic": TRAFFIC_PER_PAIR * sum(write_pairs) / max(1, len(write_pairs)),
-                     "traffic_note": "bytes per launch, scaled by pairs written from an ncu "
+                     "traffic": (TRAFFIC_PER_PAIR * sum(write_pairs) / max(1, len(write_pairs))
+                                 if TRAFFIC_PER_PAIR else None),
+                     "traffic_note": "DRAM bytes per launch, scaled by pairs written from an ncu "
                                      "capture of the same workload at scale 0.15",
                      "peak_source": peak_src,
-                     "bytes_per_launch": "8*d*(updates in chunk) + 8*d*n + 8*(pairs in chunk)",
-                     "note": "the HBM-bound kernel of the step; the count pass (about as long, "
-                             "ALU-bound) is reported in roofline_count",
+                     "bytes_per_launch": "8*(pairs in chunk): each pair written once",
+                     "note": "the HBM-bound kernel of the step; the whole query and the whole "
+                             "step are in roofline_query and roofline_step, the ALU-bound count "
+                             "pass in roofline_count",
                      "write_ms_per_step": 1e3 * write_s / args.steps},
-        "roofline_count": count_roofline(tests[0], d, count_ms, args.steps),
+        "roofline_query": {"bound": "hbm", "what": "ddm_plan + ddm_write_ordered (update sort, "
+                                                    "count pass, scans, write pass)",
+                           "achieved": qbytes / q_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": qbytes / q_s / 1e9 / hbm_peak, "peak_source": peak_src,
+                           "bytes": qbytes, "ms": 1e3 * q_s,
+                           "bytes_formula": "8*d*(n+m) + 8*K"},
+        "roofline_step": {"bound": "hbm", "what": "ms_per_step (build + plan + write)",
+                          "achieved": sbytes / step_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                          "frac": sbytes / step_s / 1e9 / hbm_peak, "peak_source": peak_src,
+                          "bytes": sbytes, "bytes_formula": "8*d*(n+m) + 8*K + 36*n"},
+        "roofline_count": count_roofline(tests[0], d, count_ms, args.steps, n_sms,
+                                         clocks["sm_mhz"] if clocks else None),
         "phases_ms_per_step": {
             "build_and_count": sum(a.elapsed_time(b) for a, b in plan_ms) / args.steps,
             "write": 1e3 * write_s / args.steps,
