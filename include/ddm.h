@@ -396,6 +396,21 @@ int ddm_set_replay_budget(ddm_ctx *ctx, uint64_t bytes);
  * DDM_ERR_ARG outside these ranges. */
 int ddm_set_tuning(ddm_ctx *ctx, int str_shift, uint32_t ctas_per_sm, uint32_t replay);
 
+/* Update-id base for sharded matching (Section IV, "Parallelizing ITM":
+ * queries are independent, so one problem's update set can be split into
+ * contiguous ranges matched on different GPUs against the same
+ * subscriptions).  Every pair this context writes afterwards carries update
+ * id base + j for its update at local position j: ddm_write,
+ * ddm_write_ordered, ddm_match and ddm_match_range without DDM_SWAP_ROLES,
+ * and ddm_match_moved without ids.  The shard holding global updates
+ * [base, base + m) thus writes the same pairs, in the same order, as one
+ * ddm_match over the whole update set writes for those updates.  Not applied
+ * to the compressed output (subscription ids only), to ddm_plan_order's
+ * order (local ids), to batched calls or to swapped roles.  Default 0; a
+ * write whose base + m exceeds 2^32 returns DDM_ERR_ARG.  DDM_ERR_ARG for a
+ * NULL context.  The paper has no counterpart. */
+int ddm_set_update_id_base(ddm_ctx *ctx, uint32_t base);
+
 /* Testing aid: make device workspace allocations that would bring the
  * context's total above `bytes` fail with DDM_ERR_NOMEM (0 = no limit). */
 int ddm_debug_set_alloc_limit(ddm_ctx *ctx, uint64_t bytes);

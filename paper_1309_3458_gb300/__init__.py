@@ -70,6 +70,7 @@ SIGNATURES = {
     "ddm_debug_set_alloc_limit": (_i, [_vp, _u64]),
     "ddm_set_replay_budget": (_i, [_vp, _u64]),
     "ddm_set_tuning": (_i, [_vp, _i, _u32, _u32]),
+    "ddm_set_update_id_base": (_i, [_vp, _u32]),
     "ddm_debug_launch_count": (_u64, []),
     "ddm_debug_wait_timeout": (_i, [_vp, _u32, _vp]),
     "ddm_scan_counts_noalloc": (_i, [_vp, _u32, _vp, _vp]),
@@ -433,6 +434,14 @@ def ddm_set_tuning(ctx: int, str_shift: int = 0, ctas_per_sm: int = 8, replay: i
     """Speed-only knobs: re-sort group shift, CTAs per SM of the packet
     kernels, replay on (1) or off (0).  Results never depend on them."""
     _check(lib().ddm_set_tuning(ctx, str_shift, ctas_per_sm, replay), "ddm_set_tuning")
+
+
+def ddm_set_update_id_base(ctx: int, base: int) -> None:
+    """Add `base` to every update id the context writes from now on (a shard
+    of updates [base, base + m) of a larger problem); see include/ddm.h."""
+    if not 0 <= base < (1 << 32):
+        raise ValueError("the update-id base must fit 32 bits")
+    _check(lib().ddm_set_update_id_base(ctx, base), "ddm_set_update_id_base")
 
 
 def ddm_set_replay_budget(ctx: int, nbytes: int) -> None:

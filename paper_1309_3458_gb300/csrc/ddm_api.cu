@@ -64,6 +64,7 @@ struct ddm_ctx {
   int str_shift = 0;            // added to the re-sort group exponents
   uint32_t ctas_per_sm = 8;     // CTAs per SM of the packet kernels
   bool replay_on = true;        // record / replay write pass allowed
+  uint32_t upd_base = 0;        // added to update ids in written pairs (ddm_set_update_id_base)
 
   bool built = false;
   bool attached = false;        // tree borrowed from another context (ddm_attach)
@@ -464,8 +465,12 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
 }
 
 // Write pass for updates with ids in [begin, end), laid out by update id.
+// Global update ids (update-id base + local id) must fit 32 bits.
+bool base_fits(const ddm_ctx* c) { return (uint64_t)c->upd_base + c->m <= (1ull << 32); }
+
 int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
                 cudaStream_t s, const uint32_t* qids = nullptr) {
+  if (!qids && !c->swapped && !c->bv.count && !base_fits(c)) return DDM_ERR_ARG;
   if (end > begin && c->tree.n > 0) {
     QueryView q = query_view(c);
     if (begin != 0 || end != c->m) {
@@ -483,6 +488,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
     w.by_pos = false;
     w.swap = c->swapped;
     w.qids = qids;
+    w.qbase = (c->swapped || c->bv.count) ? 0u : c->upd_base;
     w.b_idx = begin;
     w.e_idx = end;
     w.pairs = pairs;
@@ -503,6 +509,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
 // Write pass for the plan positions [pb, pe), laid out in plan order.
 int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, uint64_t capacity,
                         cudaStream_t s, uint32_t* ids = nullptr) {
+  if (!ids && !base_fits(c)) return DDM_ERR_ARG;
   if (pe > pb && c->tree.n > 0) {
     QueryView q = query_view(c);
     q.first = pb;
@@ -510,6 +517,7 @@ int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, u
     WriteView w{};
     w.start = static_cast<const unsigned long long*>(c->pos_offsets.p);
     w.by_pos = true;
+    w.qbase = c->upd_base;
     w.b_idx = pb;
     w.e_idx = pe;
     w.pairs = pairs;
@@ -611,6 +619,12 @@ int ddm_set_tuning(ddm_ctx* c, int str_shift, uint32_t ctas_per_sm, uint32_t rep
   c->str_shift = str_shift;
   c->ctas_per_sm = ctas_per_sm;
   c->replay_on = replay != 0;
+  return DDM_OK;
+}
+
+int ddm_set_update_id_base(ddm_ctx* c, uint32_t base) {
+  if (!c) return DDM_ERR_ARG;
+  c->upd_base = base;
   return DDM_OK;
 }
 

@@ -64,7 +64,8 @@ struct WriteView {
   const unsigned long long* start;
   bool by_pos;
   bool swap;  // roles swapped: the tree holds the updates, queries are subscriptions
-  const uint32_t* qids;  // optional: id written for query q is qids[q] (else q)
+  const uint32_t* qids;  // optional: id written for query q is qids[q] (else q + qbase)
+  uint32_t qbase;        // added to every update id written (a shard's first global id)
   uint32_t b_idx, e_idx;
   ddm_pair* pairs;
   uint32_t* ids;  // when set: only each pair's subscription id is written, here, and pairs is unused

@@ -215,7 +215,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
     }
     // Position range of the subscriptions this query may match, and the
     // update id written into pairs (instance-local when batched).
-    uint32_t r_lo = 0, r_hi = (uint32_t)n, Qout = Q;
+    uint32_t r_lo = 0, r_hi = (uint32_t)n, Qout = WRITE ? Q + w.qbase : Q;
     if (WRITE && w.qids && valid) Qout = w.qids[Q];
     if (BATCH && valid) {
       const uint32_t b = bv.q_inst[pos];
@@ -682,7 +682,7 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     if (FILTER_ID) valid = valid && Q >= idb && Q < ide;
     Cursor out = 0;
     if (valid) out = (Cursor)(w.start[w.by_pos ? pos : Q] - base0);
-    uint32_t Qout = Q, sub_base = 0;
+    uint32_t Qout = Q + w.qbase, sub_base = 0;
     if (w.qids && valid) Qout = w.qids[Q];
     if (BATCH && valid) {
       const uint32_t b = bv.q_inst[pos];
