@@ -7,9 +7,10 @@
   tree (OpenMP), plus the whole pair set where it is small.
 * d = 3, N = 1e7, clustered (about 4.4e10 pairs, more than device memory):
   run exactly as the benchmark runs it -- plan, then ordered chunks of a
-  64 GB pair buffer.  Sampled updates are checked pair by pair against brute
-  force, a larger sample by count and digest against the oracle's interval
-  tree, and properties that hold at any size are checked on every chunk.
+  pair buffer (chunks alternating above and below 2^32 pairs).  10^4 random
+  updates and whole dense packets are checked pair by pair against brute
+  force, 10^4 more by count and digest against the oracle's interval tree,
+  and properties that hold at any size are checked on every chunk.
   The compressed output (subscription ids only) of more than 2^32 pairs in
   one call equals the pair list's subscription column.
 """
@@ -67,7 +68,50 @@ def test_d2_full_counts_and_digests(ctx, name):
         assert np.array_equal(np.sort(keys(pu, ps)), np.sort(keys(ou, os_)))
 
 
+# Brute force (Alg. 2) on the sampled updates runs in a spawned process pool:
+# each worker regenerates the seeded subscriptions once and takes chunks of
+# the sampled updates.
+_BF_SUBS = None
+
+
+def _bf_init(name):
+    global _BF_SUBS
+    a = W.make(name)
+    _BF_SUBS = (a[2], a[3])
+
+
+def _bf_chunk(args):
+    ulo_c, uhi_c = args
+    _, counts, _, _, ps = oracle.bf(ulo_c, uhi_c, *_BF_SUBS)
+    return counts, ps
+
+
+def brute_force_sets(name, ulo, uhi, ids):
+    """Per sampled update, its subscription ids in ascending order (BF)."""
+    import multiprocessing as mp
+    chunks = np.array_split(np.asarray(ids), max(1, 4 * THREADS))
+    work = [(np.ascontiguousarray(ulo[:, c]), np.ascontiguousarray(uhi[:, c])) for c in chunks if len(c)]
+    with mp.get_context("spawn").Pool(THREADS, initializer=_bf_init, initargs=(name,)) as pool:
+        res = pool.map(_bf_chunk, work)
+    out = {}
+    for c, (counts, ps) in zip([c for c in chunks if len(c)], res):
+        at = np.concatenate([[0], np.cumsum(counts.astype(np.int64))])
+        for i, j in enumerate(c):
+            out[int(j)] = ps[at[i]:at[i + 1]]
+    return out
+
+
 def test_d3_clustered_full_size_chunked(ctx):
+    """Run as the benchmark runs it, checked on a sample of 10^4 random
+    updates plus whole 32-query packets pair by pair against brute force
+    (Alg. 2), and 10^4 more by count and digest against the oracle's
+    interval tree.  The packets are the densest of the plan (by pairs per
+    packet: their leaves are tested with the swapped loops, lane = query,
+    which runs for most of this workload's tests) and some chosen at random.
+    Chunks alternate between a pair buffer above 2^32 pairs (64-bit output
+    positions in the write kernel) and one below (32-bit positions), so both
+    write kernels expand sampled updates.  Every query touches leaves of
+    several size classes of the tree order."""
     import torch
     name = "clustered_d3_N1e7_a100"
     arrays = W.make(name)
@@ -88,19 +132,26 @@ def test_d3_clustered_full_size_chunked(ctx):
     assert np.array_equal(np.diff(ooff_h), counts[order_h])
 
     rng = np.random.default_rng(2024)
-    exact = np.sort(rng.choice(m, 64, replace=False))           # pair by pair vs brute force
-    sampled = np.sort(rng.choice(m, 2000, replace=False))       # count + digest vs ITM
+    packets = m // 32
+    per_packet = ooff_h[32 * np.arange(packets + 1)[1:]] - ooff_h[32 * np.arange(packets)]
+    dense = np.argsort(per_packet)[-8:]
+    chosen = np.concatenate([dense, rng.choice(packets, 8, replace=False)])
+    packet_ids = order_h[(32 * chosen[:, None] + np.arange(32)[None, :]).ravel()]
+    exact = np.unique(np.concatenate([rng.choice(m, 10_000, replace=False), packet_ids]))
+    sampled = np.sort(rng.choice(m, 10_000, replace=False))     # count + digest vs ITM
     pos_of = np.empty(m, np.int64)
     pos_of[order_h] = np.arange(m)
     want_pos = {int(pos_of[j]): int(j) for j in np.concatenate([exact, sampled])}
 
-    cap = int(64e9) // 8
+    cap = int(64e9) // 8                 # above 2^32 pairs: 64-bit positions
+    small_cap = int(16e9) // 8           # below: 32-bit positions
     buf = torch.empty((cap, 2), dtype=torch.int32, device="cuda")
     got = {}
-    b, written = 0, 0
+    b, written, chunk = 0, 0, 0
     while b < m:
-        e = ddm.ddm_chunk_end_ordered(ctx, b, cap)
-        k = ddm.ddm_write_ordered(ctx, b, e, buf)
+        cap_i = cap if chunk % 2 == 0 else small_cap
+        e = ddm.ddm_chunk_end_ordered(ctx, b, cap_i)
+        k = ddm.ddm_write_ordered(ctx, b, e, buf[:cap_i])
         assert k == ooff_h[e] - ooff_h[b]
         written += k
         # properties on the whole chunk: ids in range, each update's run
@@ -127,13 +178,15 @@ def test_d3_clustered_full_size_chunked(ctx):
             assert torch.equal(sub_ids, buf[:k2, 1])
             del sub_ids
         b = e
-    assert written == K
+        chunk += 1
+    assert written == K and chunk >= 4
+    del buf
+    torch.cuda.empty_cache()
 
-    # pair by pair against brute force (Alg. 2) on single updates
+    # pair by pair against brute force (Alg. 2)
+    bf_sets = brute_force_sets(name, ulo, uhi, exact)
     for j in exact:
-        _, _, _, bu, bs = oracle.bf(np.ascontiguousarray(ulo[:, j:j + 1]),
-                                    np.ascontiguousarray(uhi[:, j:j + 1]), slo, shi)
-        assert np.array_equal(np.sort(got[int(j)]), bs), j
+        assert np.array_equal(np.sort(got[int(j)]), bf_sets[int(j)]), j
     # counts and digests against the oracle's interval tree (OpenMP)
     Ks, cs, gs = oracle.itm_count(np.ascontiguousarray(ulo[:, sampled]),
                                   np.ascontiguousarray(uhi[:, sampled]), slo, shi,
@@ -141,5 +194,3 @@ def test_d3_clustered_full_size_chunked(ctx):
     assert np.array_equal(counts[sampled], cs)
     for j, g in zip(sampled, gs):
         assert oracle.digest_of(got[int(j)]) == int(g)
-    del buf
-    torch.cuda.empty_cache()
