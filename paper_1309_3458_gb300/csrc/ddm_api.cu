@@ -32,6 +32,22 @@ struct ddm_ctx {
   uint64_t alloc_limit = 0;  // 0 = unlimited (testing aid)
   uint64_t allocated = 0;
 
+  // Workspace comes from the context's own memory pool, allocated and freed
+  // in stream order on the calling stream: growing a buffer never
+  // synchronises the device (cudaMalloc / cudaFree would), so one context's
+  // growth does not stall the work of others.  The pool keeps what is freed
+  // (no release threshold) for the next growth.
+  cudaMemPool_t pool = nullptr;
+  cudaStream_t cur = nullptr;      // stream of the call in progress
+  bool capturing = false;          // that stream is being captured into a graph
+  // Calls may come on different streams: each call records `done` on its
+  // stream when it has enqueued its work, and a call on another stream first
+  // waits for it, so the context's buffers are never used by two streams at
+  // once and a stream-ordered free never overtakes earlier work.
+  cudaEvent_t done = nullptr;
+  cudaStream_t last = nullptr;
+  bool done_pending = false;
+
   Status* st_dev = nullptr;
   Status* st_host = nullptr;  // pinned mirror
 
@@ -97,11 +113,44 @@ class DeviceGuard {
   bool ok_ = false, switched_ = false;
 };
 
+// Orders a call's work after the context's previous call (made on another
+// stream) and marks its end; binds the call's stream for ensure().  A stream
+// being captured into a graph is neither waited on nor recorded (its work runs
+// only when the graph is launched); growth is refused while capturing.
+class StreamUse {
+ public:
+  StreamUse(ddm_ctx* c, cudaStream_t s) : c_(c), s_(s) {
+    cudaStreamCaptureStatus st = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &st) != cudaSuccess) {
+      cudaGetLastError();
+      st = cudaStreamCaptureStatusNone;
+    }
+    capturing_ = st != cudaStreamCaptureStatusNone;
+    if (!capturing_ && c->done_pending && c->last != s) cudaStreamWaitEvent(s, c->done, 0);
+    c->cur = s;
+    c->capturing = capturing_;
+  }
+  ~StreamUse() {
+    if (!capturing_ && cudaEventRecord(c_->done, s_) == cudaSuccess) {
+      c_->done_pending = true;
+      c_->last = s_;
+    }
+    cudaGetLastError();
+    c_->capturing = false;
+  }
+
+ private:
+  ddm_ctx* c_;
+  cudaStream_t s_;
+  bool capturing_ = false;
+};
+
 int ensure(ddm_ctx* c, DevBuf& b, size_t bytes) {
   if (bytes <= b.cap) return DDM_OK;
+  if (c->capturing) return DDM_ERR_NOMEM;  // a graph cannot own the workspace
   size_t want = bytes + bytes / 4;  // headroom against regrowth
   if (b.p) {
-    cudaFree(b.p);
+    cudaFreeAsync(b.p, c->cur);  // after the work already enqueued on this stream
     c->allocated -= b.cap;
     b.p = nullptr;
     b.cap = 0;
@@ -110,8 +159,8 @@ int ensure(ddm_ctx* c, DevBuf& b, size_t bytes) {
     want = bytes;
     if (c->allocated + want > c->alloc_limit) return DDM_ERR_NOMEM;
   }
-  if (cudaMalloc(&b.p, want) != cudaSuccess) {
-    cudaGetLastError();  // clear the sticky-free allocation error
+  if (cudaMallocFromPoolAsync(&b.p, want, c->pool, c->cur) != cudaSuccess) {
+    cudaGetLastError();  // clear the allocation error
     b.p = nullptr;
     return DDM_ERR_NOMEM;
   }
@@ -128,7 +177,7 @@ float2* aos_buffer(ddm_ctx* c, int d, uint32_t cnt) {
 }
 
 void release(DevBuf& b) {
-  if (b.p) cudaFree(b.p);
+  if (b.p) cudaFreeAsync(b.p, nullptr);
   b.p = nullptr;
   b.cap = 0;
 }
@@ -575,7 +624,16 @@ int ddm_create(ddm_ctx** out, int device) {
     if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) c->replay_budget = total_b / 4;
     cudaGetLastError();
   }
-  if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+  cudaMemPoolProps props{};
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = device;
+  const uint64_t keep_all = ~0ull;
+  if (cudaMemPoolCreate(&c->pool, &props) != cudaSuccess ||
+      cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, (void*)&keep_all) !=
+          cudaSuccess ||
+      cudaEventCreateWithFlags(&c->done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
       cudaMalloc(&c->st_dev, sizeof(Status)) != cudaSuccess ||
       cudaMallocHost(&c->st_host, sizeof(Status)) != cudaSuccess ||
       cudaMallocHost((void**)&c->rec_hint, 3 * sizeof(uint32_t)) != cudaSuccess) {
@@ -600,6 +658,9 @@ int ddm_destroy(ddm_ctx* c) {
                     &c->blk_list, &c->blk_counter, &c->inst_s, &c->inst_u, &c->bglog2,
                     &c->bngroups, &c->bgbase, &c->cls_hist, &c->cls_off, &c->probe, &c->aos})
     release(*b);
+  cudaDeviceSynchronize();  // the stream-ordered frees above have run
+  if (c->pool) cudaMemPoolDestroy(c->pool);
+  if (c->done) cudaEventDestroy(c->done);
   if (c->st_dev) cudaFree(c->st_dev);
   if (c->st_host) cudaFreeHost(c->st_host);
   if (c->rec_hint) cudaFreeHost((void*)c->rec_hint);
@@ -633,6 +694,7 @@ int ddm_debug_wait_timeout(ddm_ctx* c, uint32_t polls, void* stream) {
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(ensure(c, c->probe, sizeof(uint32_t)));
   DDM_CUDA(cudaMemsetAsync(c->probe.p, 0, sizeof(uint32_t), s));
   DDM_TRY(reset_status(c, s));
@@ -654,6 +716,7 @@ int ddm_build(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n,
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(build_async(c, d, slo, shi, n, s));
   DDM_TRY(sync_status(c, s));
@@ -670,6 +733,7 @@ int ddm_plan(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(plan_async(c, ulo, uhi, m, flags, true, s));
   if (offsets)
@@ -691,6 +755,7 @@ int ddm_write(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
   DDM_TRY(sync_status(c, s));
@@ -705,6 +770,7 @@ int ddm_chunk_end(ddm_ctx* c, uint32_t begin, uint64_t capacity, uint32_t* upd_e
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_CUDA(launch_chunk_end(static_cast<const unsigned long long*>(c->offsets.p), c->m, begin,
                             capacity, c->st_dev, s));
   DDM_TRY(sync_status(c, s));
@@ -721,6 +787,7 @@ int ddm_plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, u
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(plan_async(c, ulo, uhi, m, flags, true, s));
   return DDM_OK;
@@ -734,6 +801,7 @@ int ddm_write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, u
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   // keep the plan's error bits; the write sets K (and the capacity bit)
   DDM_TRY(write_async(c, begin, end, pairs, capacity, s));
   if (k_dev)
@@ -760,6 +828,7 @@ int ddm_match_moved(ddm_ctx* c, const float* lo, const float* hi, uint32_t k, co
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(plan_async(c, lo, hi, k, flags & DDM_OPEN, true, s));
   const bool was = c->swapped;
@@ -781,6 +850,7 @@ int ddm_pair_offsets_async(ddm_ctx* c, const uint64_t* upd_off, uint32_t count, 
   if (!c->planned) return DDM_ERR_STATE;
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
+  StreamUse use(c, static_cast<cudaStream_t>(stream));
   DDM_CUDA(launch_gather_offsets(static_cast<const unsigned long long*>(c->offsets.p), c->m,
                                  reinterpret_cast<const unsigned long long*>(upd_off), count,
                                  reinterpret_cast<unsigned long long*>(pair_off),
@@ -796,6 +866,7 @@ int ddm_write_ordered(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, ddm_pair
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(write_ordered_async(c, pos_begin, pos_end, pairs, capacity, s));
   DDM_TRY(sync_status(c, s));
@@ -811,6 +882,7 @@ int ddm_write_ordered_ids(ddm_ctx* c, uint32_t pos_begin, uint32_t pos_end, uint
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(write_ordered_async(c, pos_begin, pos_end, nullptr, capacity, s, sub_ids));
   DDM_TRY(sync_status(c, s));
@@ -826,6 +898,7 @@ int ddm_chunk_end_ordered(ddm_ctx* c, uint32_t pos_begin, uint64_t capacity, uin
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_CUDA(launch_chunk_end(static_cast<const unsigned long long*>(c->pos_offsets.p), c->m,
                             pos_begin, capacity, c->st_dev, s));
   DDM_TRY(sync_status(c, s));
@@ -840,6 +913,7 @@ int ddm_plan_order(ddm_ctx* c, uint32_t* order, uint64_t* order_offsets, void* s
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   if (order && c->m)
     DDM_CUDA(cudaMemcpyAsync(order, c->qid.p, sizeof(uint32_t) * c->m, cudaMemcpyDeviceToDevice, s));
   if (order_offsets)
@@ -869,6 +943,7 @@ static int match_impl(ddm_ctx* c, int d, const float* ulo, const float* uhi, uin
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   DDM_TRY(build_async(c, d, slo, shi, n, s));
   c->swapped = swap;
@@ -914,6 +989,7 @@ static int batch_impl(ddm_ctx* c, int d, uint32_t count, const float* ulo, const
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(ensure(c, c->inst_s, sizeof(uint32_t) * (n ? n : 1)));
   DDM_TRY(ensure(c, c->inst_u, sizeof(uint32_t) * (m ? m : 1)));
   DDM_TRY(reset_status(c, s));
@@ -972,6 +1048,7 @@ int ddm_refit(ddm_ctx* c, const float* sub_lo, const float* sub_hi, void* stream
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   c->planned = false;
   if (c->tree.n > 0) {
@@ -1023,6 +1100,7 @@ int ddm_tree_export(ddm_ctx* c, uint32_t* order, float* node_lo, float* node_hi,
   DeviceGuard g(c->device);
   if (!g.ok()) return DDM_ERR_CUDA;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  StreamUse use(c, s);
   if (order)
     DDM_CUDA(cudaMemcpyAsync(order, c->sid.p, sizeof(uint32_t) * c->tree.n,
                              cudaMemcpyDeviceToDevice, s));
