@@ -431,9 +431,46 @@ def serving_section(seconds: float = 2.0, slots: int = 4, saturated_seconds: flo
     out["served_over_plain"] = plain_wall / sat_wall
     out.update({"workload": "d=2, 1e6 moving regions, 64 federates, 2000 req/s Poisson, "
                             "sizes log-uniform [1e3, 1e6]",
+                "policy": "rebuild the idle version every step",
                 "rebuilds": regions.rebuilds, "refits": regions.refits,
                 "slots": slots, "budget_gb": budget / 1e9, "offered_s": seconds,
                 "steps": max(r.step for r in done) if done else 0})
+
+    # The same real-time schedule under the configured in-place refit per
+    # step: refit only, and refit with a rebuild when a probe finds the
+    # refitted tree slower than `adaptive` times its post-rebuild speed.
+    out["other_policies"] = {}
+    for pname, kw in (("refit_every_step", dict(rebuild_every=0)),
+                      ("refit_every_step_rebuild_when_1.5x_slower",
+                       dict(rebuild_every=0, adaptive=1.5))):
+        g.manual_seed(2026)
+        lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
+        hi = (lo + l).contiguous()
+        state.update(lo=lo, hi=hi)
+        mg.manual_seed(7)
+        reg = S.ResidentRegions(lo, hi, **kw)
+        sched2 = S.poisson_schedule(rate=2000.0, duration=seconds, federates=64, size_lo=1000,
+                                    size_hi=1_000_000, seed=1)
+        warm2 = S.poisson_schedule(rate=2000.0, duration=0.25, federates=64, size_lo=1000,
+                                   size_hi=1_000_000, seed=3)
+        srv2 = S.Server(reg, l, slots=slots, budget_bytes=budget, pair_capacity=1 << 26)
+        try:
+            srv2.warm_up()
+            attach(warm2, warm_sets)
+            srv2.run(warm2, mover=mover, step_s=0.010)
+            attach(sched2, sched_sets)
+            t0 = time.perf_counter()
+            done2 = srv2.run(sched2, mover=mover, step_s=0.010)
+            wall2 = time.perf_counter() - t0
+        finally:
+            srv2.close()
+            reg.close()
+        o2 = S.summary(done2, wall2)
+        o2.update({"rebuilds": reg.rebuilds, "refits": reg.refits,
+                   "steps": max(r.step for r in done2) if done2 else 0})
+        if reg.tests_ratio:
+            o2["probe_tests_ratio_max"] = max(reg.tests_ratio)
+        out["other_policies"][pname] = o2
     return out
 
 

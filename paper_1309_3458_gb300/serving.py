@@ -65,16 +65,32 @@ class ResidentRegions:
 
     A movement step brings the idle version up to date and activates it,
     by an in-place refit (same order, new node bounds) or, every
-    `rebuild_every`-th step, by a full rebuild (re-sort).  A refit keeps the
+    `rebuild_every`-th step, by a full rebuild (re-sort); with `adaptive`,
+    by a refit every step followed by a rebuild when a probe finds the
+    refitted tree too slow.  A refit keeps the
     result exact, but the order ages: the regions of a leaf drift apart, its
     bounding box grows and the queries test more candidates, so the order is
     renewed periodically (`rebuild_every` = 0: refit only; 1: rebuild every
     step)."""
 
-    def __init__(self, lo, hi, keep_history: bool = False, rebuild_every: int = 1):
+    def __init__(self, lo, hi, keep_history: bool = False, rebuild_every: int = 1,
+                 adaptive: float = 0.0, probe_size: int = 4096, probe_seed: int = 99):
+        """adaptive > 0 (with rebuild_every = 0): refit every step in place, then
+        measure the refitted tree with a fixed probe update set (its (query,
+        leaf) tests per query, ddm_plan_stats); when that exceeds `adaptive`
+        times the value measured after the last rebuild, rebuild the version
+        instead (the order has aged too far)."""
         import torch
         self.d, self.n = lo.shape
         self.ctx = [ddm.ddm_create(lo.device.index or 0) for _ in range(2)]
+        self.adaptive = adaptive
+        self.probe_ctx = None
+        self.tests_ratio: List[float] = []
+        if adaptive > 0:
+            side = float((hi[:, :1] - lo[:, :1]).max().item())
+            self.probe = request_updates(probe_seed, probe_size, self.d, side, device=lo.device)
+            self.probe_ctx = ddm.ddm_create(lo.device.index or 0)
+            self.base_tests = [0.0, 0.0]
         self.pos = [(lo.clone(), hi.clone()), (lo.clone(), hi.clone())]
         self.stream = torch.cuda.Stream()
         with torch.cuda.stream(self.stream):
@@ -87,6 +103,15 @@ class ResidentRegions:
         self.history = {0: (lo.clone(), hi.clone())} if keep_history else None
         self.rebuild_every = rebuild_every
         self.rebuilds = self.refits = 0
+        if self.probe_ctx is not None:
+            for v in range(2):
+                self.base_tests[v] = self._probe(v)
+
+    def _probe(self, v) -> float:
+        """(query, leaf) tests per probe query against version v's tree."""
+        ddm.ddm_attach(self.probe_ctx, self.ctx[v])
+        ddm.ddm_plan(self.probe_ctx, self.probe[0], self.probe[1], stream=self.stream)
+        return ddm.ddm_plan_stats(self.probe_ctx) / self.probe[0].shape[1]
 
     def acquire(self):
         with self.cv:
@@ -119,6 +144,14 @@ class ResidentRegions:
                     ddm.ddm_refit(self.ctx[idle], self.pos[idle][0], self.pos[idle][1],
                                   stream=self.stream)
                     self.refits += 1
+                    if self.probe_ctx is not None:
+                        ratio = self._probe(idle) / max(self.base_tests[idle], 1e-9)
+                        self.tests_ratio.append(ratio)
+                        if ratio > self.adaptive:
+                            ddm.ddm_build(self.ctx[idle], self.pos[idle][0], self.pos[idle][1],
+                                          stream=self.stream)
+                            self.rebuilds += 1
+                            self.base_tests[idle] = self._probe(idle)
             self.step_of[idle] = step_index
             self.active = idle
             if self.history is not None:
@@ -127,6 +160,9 @@ class ResidentRegions:
     def close(self):
         for c in self.ctx:
             ddm.ddm_destroy(c)
+        if self.probe_ctx is not None:
+            ddm.ddm_destroy(self.probe_ctx)
+            self.probe_ctx = None
 
 
 @dataclass
