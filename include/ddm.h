@@ -396,6 +396,20 @@ int ddm_set_replay_budget(ddm_ctx *ctx, uint64_t bytes);
  * DDM_ERR_ARG outside these ranges. */
 int ddm_set_tuning(ddm_ctx *ctx, int str_shift, uint32_t ctas_per_sm, uint32_t replay);
 
+/* Tiling of the query kernels (speed only, never results; the autotuner in
+ * the Python package picks it per workload):
+ *  queries_per_packet -- 16 or 32 queries walk the tree together in one warp
+ *                        (default 32; the leaves keep 32 subscriptions, one
+ *                        per lane);
+ *  swap_min           -- 1..33: a leaf met by at least this many of a
+ *                        packet's queries is tested with the loops swapped
+ *                        (lane = query, loop over the leaf's subscriptions);
+ *                        33 = never (default 24).
+ * Changing queries_per_packet drops the current plan (its records are laid
+ * out by packet).  DDM_ERR_ARG outside these values or for a NULL context.
+ * The paper has no counterpart (Section IV's queries run one per thread). */
+int ddm_set_tiling(ddm_ctx *ctx, uint32_t queries_per_packet, uint32_t swap_min);
+
 /* Update-id base for sharded matching (Section IV, "Parallelizing ITM":
  * queries are independent, so one problem's update set can be split into
  * contiguous ranges matched on different GPUs against the same

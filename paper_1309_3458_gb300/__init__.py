@@ -71,6 +71,7 @@ SIGNATURES = {
     "ddm_set_replay_budget": (_i, [_vp, _u64]),
     "ddm_set_tuning": (_i, [_vp, _i, _u32, _u32]),
     "ddm_set_update_id_base": (_i, [_vp, _u32]),
+    "ddm_set_tiling": (_i, [_vp, _u32, _u32]),
     "ddm_debug_launch_count": (_u64, []),
     "ddm_debug_wait_timeout": (_i, [_vp, _u32, _vp]),
     "ddm_scan_counts_noalloc": (_i, [_vp, _u32, _vp, _vp]),
@@ -434,6 +435,13 @@ def ddm_set_tuning(ctx: int, str_shift: int = 0, ctas_per_sm: int = 8, replay: i
     """Speed-only knobs: re-sort group shift, CTAs per SM of the packet
     kernels, replay on (1) or off (0).  Results never depend on them."""
     _check(lib().ddm_set_tuning(ctx, str_shift, ctas_per_sm, replay), "ddm_set_tuning")
+
+
+def ddm_set_tiling(ctx: int, queries_per_packet: int = 32, swap_min: int = 24) -> None:
+    """Speed-only tiling of the query kernels: 16 or 32 queries per warp, and
+    the number of a packet's queries on a leaf from which the count pass swaps
+    its loops (33 = never).  Results never depend on it."""
+    _check(lib().ddm_set_tiling(ctx, queries_per_packet, swap_min), "ddm_set_tiling")
 
 
 def ddm_set_update_id_base(ctx: int, base: int) -> None:

@@ -1,8 +1,14 @@
-"""Autotuner for the library's tuning knobs (``ddm_set_tuning``).
+"""Autotuner for the library's tuning knobs (``ddm_set_tuning`` and
+``ddm_set_tiling``).
 
 The knobs change speed only, never results: the re-sort group exponent shift
-of the tree order, the CTAs per SM of the persistent query kernels, and
-whether the write pass replays the count pass's records or walks the tree.
+of the tree order, the CTAs per SM of the persistent query kernels, whether
+the write pass replays the count pass's records or walks the tree, the
+queries per warp (16 or 32 per packet: the tile is queries x the leaf's 32
+subscriptions), and the number of a packet's queries on a leaf from which the
+count pass swaps its loops (lane = query instead of lane = subscription).
+The tree's fan-out stays 32: one lane per child, so a node's children are
+tested by one coalesced load and one ballot.
 ``autotune`` times a caller-supplied run (one complete match through the C
 ABI) under each candidate with CUDA events and keeps the fastest; the work
 itself always runs in the library's kernels.
@@ -14,7 +20,19 @@ from typing import Callable, Dict, Iterable, List, Optional, Tuple
 
 import paper_1309_3458_gb300 as ddm
 
-DEFAULT_SPACE = {"str_shift": (-1, 0, 1), "ctas_per_sm": (4, 8), "replay": (1, 0)}
+DEFAULT_SPACE = {"str_shift": (-1, 0, 1), "ctas_per_sm": (4, 8), "replay": (1, 0),
+                 "queries_per_packet": (32, 16), "swap_min": (16, 24, 33)}
+TUNING = ("str_shift", "ctas_per_sm", "replay")
+TILING = ("queries_per_packet", "swap_min")
+DEFAULTS = {"str_shift": 0, "ctas_per_sm": 8, "replay": 1, "queries_per_packet": 32,
+            "swap_min": 24}
+
+
+def apply(ctx: int, cand: Dict[str, int]) -> None:
+    """Set a candidate (missing knobs take their defaults) on a context."""
+    full = dict(DEFAULTS, **cand)
+    ddm.ddm_set_tuning(ctx, **{k: full[k] for k in TUNING})
+    ddm.ddm_set_tiling(ctx, **{k: full[k] for k in TILING})
 
 
 def candidates(space: Optional[Dict[str, Iterable]] = None) -> List[Dict[str, int]]:
@@ -32,7 +50,7 @@ def autotune(ctx: int, run: Callable[[], None], space=None, reps: int = 3,
     stream = stream or torch.cuda.current_stream()
     table = []
     for cand in candidates(space):
-        ddm.ddm_set_tuning(ctx, **cand)
+        apply(ctx, cand)
         run()  # warm-up: sizes workspace and record arena for this candidate
         times = []
         for _ in range(reps):
@@ -47,5 +65,5 @@ def autotune(ctx: int, run: Callable[[], None], space=None, reps: int = 3,
         table.append((times[len(times) // 2], cand))
     table.sort(key=lambda x: x[0])
     best = table[0][1]
-    ddm.ddm_set_tuning(ctx, **best)
+    apply(ctx, best)
     return best, table

@@ -81,6 +81,10 @@ struct ddm_ctx {
   uint32_t ctas_per_sm = 8;     // CTAs per SM of the packet kernels
   bool replay_on = true;        // record / replay write pass allowed
   uint32_t upd_base = 0;        // added to update ids in written pairs (ddm_set_update_id_base)
+  // tiling (ddm_set_tiling): log2 of the queries per packet, and the number of
+  // a packet's queries meeting a leaf from which the count pass swaps the loops
+  uint32_t qpp_log2 = 5;
+  uint32_t tmin = 24;
 
   bool built = false;
   bool attached = false;        // tree borrowed from another context (ddm_attach)
@@ -399,6 +403,11 @@ int packet_sms(const ddm_ctx* c) {
   return v > 0 ? v : 1;
 }
 
+// Packets of the count pass (and of its records) covering positions [0, m).
+uint32_t packets_of(const ddm_ctx* c, uint32_t m) {
+  return (uint32_t)(((uint64_t)m + (1u << c->qpp_log2) - 1u) >> c->qpp_log2);
+}
+
 QueryView query_view(ddm_ctx* c) {
   QueryView q{};
   q.m = c->m;
@@ -407,6 +416,8 @@ QueryView query_view(ddm_ctx* c) {
   q.list = nullptr;
   q.first = 0;
   q.nq = c->m;
+  q.qpp_log2 = c->qpp_log2;
+  q.tmin = c->tmin;
   return q;
 }
 
@@ -430,7 +441,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   c->m = m;
   c->arena = RecordArena{};
   if (record && c->replay_on && m > 0 && c->tree.n > 0 && c->replay_budget > 0) {
-    const uint32_t packets = (m + 31) / 32;
+    const uint32_t packets = packets_of(c, m);
     // bytes per block: records (three words each), next/count/packet/list entries
     const uint64_t per_block = (uint64_t)kRecBlock * 3 * sizeof(uint32_t) + 4 * sizeof(uint32_t);
     // Blocks the arena holds now, and what the latest recorded pass needed.
@@ -499,7 +510,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   DDM_CUDA(launch_scan(counts_pos, m, pos_offsets, sums, nullptr, s));
   DDM_CUDA(launch_scan(counts, m, offsets, sums, c->st_dev, s));
   if (c->arena.max_blocks) {  // plan-order list of the record blocks
-    const uint32_t packets = (m + 31) / 32;
+    const uint32_t packets = packets_of(c, m);
     DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets, c->arena.pkt_off, sums, nullptr, s));
     DDM_CUDA(launch_block_list(c->arena, packets, s));
   }
@@ -545,7 +556,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
     auto* work = static_cast<uint32_t*>(c->work.p);
     if (c->arena.max_blocks) {
       const bool full = begin == 0 && end == c->m;
-      DDM_CUDA(launch_replay(c->tree, query_view(c), c->bv, c->arena, w, 0, (c->m + 31) / 32, 0, c->m,
+      DDM_CUDA(launch_replay(c->tree, query_view(c), c->bv, c->arena, w, 0, packets_of(c, c->m), 0, c->m,
                              !full, begin, end, work, c->st_dev, c->sms, s));
     }
     DDM_CUDA(launch_write(c->tree, q, c->bv, c->flags, w, c->arena, work, c->st_dev, packet_sms(c), s));
@@ -574,7 +585,7 @@ int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, u
     w.capacity = capacity;
     auto* work = static_cast<uint32_t*>(c->work.p);
     if (c->arena.max_blocks)
-      DDM_CUDA(launch_replay(c->tree, q, c->bv, c->arena, w, pb / 32, (pe + 31) / 32, pb, pe, false, 0, 0,
+      DDM_CUDA(launch_replay(c->tree, q, c->bv, c->arena, w, pb >> c->qpp_log2, packets_of(c, pe), pb, pe, false, 0, 0,
                              work, c->st_dev, c->sms, s));
     DDM_CUDA(launch_write(c->tree, q, c->bv, c->flags, w, c->arena, work, c->st_dev, packet_sms(c), s));
   } else {
@@ -680,6 +691,17 @@ int ddm_set_tuning(ddm_ctx* c, int str_shift, uint32_t ctas_per_sm, uint32_t rep
   c->str_shift = str_shift;
   c->ctas_per_sm = ctas_per_sm;
   c->replay_on = replay != 0;
+  return DDM_OK;
+}
+
+int ddm_set_tiling(ddm_ctx* c, uint32_t queries_per_packet, uint32_t swap_min) {
+  if (!c || (queries_per_packet != 16 && queries_per_packet != 32) || swap_min < 1 ||
+      swap_min > 33)
+    return DDM_ERR_ARG;
+  const uint32_t lg = queries_per_packet == 16 ? 4u : 5u;
+  if (lg != c->qpp_log2) c->planned = false;  // the plan's records use its packets
+  c->qpp_log2 = lg;
+  c->tmin = swap_min;
   return DDM_OK;
 }
 

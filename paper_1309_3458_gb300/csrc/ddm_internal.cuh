@@ -55,6 +55,8 @@ struct QueryView {
   const uint32_t* list;           // optional subset of sorted positions (ranges)
   uint32_t first;                 // without list: run positions first .. first+nq-1
   uint32_t nq;                    // number of queries to run
+  uint32_t qpp_log2;              // log2 of the queries per packet (4 or 5: 16 or 32)
+  uint32_t tmin;                  // count pass: swapped leaf loops from this many queries
 };
 
 // Where the write pass puts each query's pairs: query j's pairs start at

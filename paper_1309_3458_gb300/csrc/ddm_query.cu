@@ -44,12 +44,6 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
-// Count pass: a leaf tested by at least this many of the packet's queries is
-// evaluated with the loops swapped (lane = query, loop over the leaf's 32
-// subscriptions), which costs the same whatever the number of queries.
-#ifndef DDM_TRANSPOSE_MIN
-#define DDM_TRANSPOSE_MIN 24
-#endif
 // Resident 256-thread blocks per SM the packet kernels are compiled for.
 #ifndef DDM_PACKET_MIN_BLOCKS
 #define DDM_PACKET_MIN_BLOCKS 4
@@ -198,16 +192,17 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
     if (need > w.capacity) return;
   }
 
-  const uint32_t npk = (q.nq + 31u) >> 5;
+  const uint32_t qpp = 1u << q.qpp_log2;  // queries per packet: 16 or 32
+  const uint32_t npk = (q.nq + qpp - 1u) >> q.qpp_log2;
   for (;;) {
     uint32_t p = 0;
     if (lane == 0) p = atomicAdd(work, 1u);
     p = __shfl_sync(0xffffffffu, p, 0);
     if (p >= npk) break;
 
-    // ---- the packet: up to 32 queries, one per lane ----
-    const uint32_t idx = p * 32u + lane;
-    const bool valid = idx < q.nq;
+    // ---- the packet: up to qpp queries, one per lane ----
+    const uint32_t idx = (p << q.qpp_log2) + lane;
+    const bool valid = (uint32_t)lane < qpp && idx < q.nq;
     uint32_t pos = 0, Q = 0;
     if (valid) {
       pos = q.list ? q.list[idx] : q.first + idx;
@@ -301,7 +296,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
         uint32_t my_sid = 0;
         if (WRITE && iv) my_sid = t.sid[i];
         uint32_t my_hb = 0;  // count pass: this lane's query's hit mask in the leaf
-        if (!WRITE && __popc(qm) >= DDM_TRANSPOSE_MIN) {
+        if (!WRITE && __popc(qm) >= q.tmin) {
           // Swapped loops: stage the leaf's subscriptions, then every lane
           // tests its own query against all 32 of them (the same segment
           // tests of Alg. 1 in every dimension, in the opposite order).
@@ -675,8 +670,8 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     if (i >= i1) break;
     const uint32_t blk = ra.blk_list[i];
     const uint32_t p = ra.blk_pkt[blk];
-    const uint32_t pos = p * 32u + lane;
-    bool valid = pos >= pb && pos < pe;
+    const uint32_t pos = (p << q.qpp_log2) + lane;
+    bool valid = (uint32_t)lane < (1u << q.qpp_log2) && pos >= pb && pos < pe;
     uint32_t Q = 0;
     if (valid) Q = q.qid[pos];
     if (FILTER_ID) valid = valid && Q >= idb && Q < ide;
@@ -775,7 +770,7 @@ cudaError_t launch_packets(const TreeView& t, const QueryView& q, const BatchVie
   cudaError_t e = cudaMemsetAsync(work, 0, sizeof(uint32_t), s);
   if (e) return e;
   const bool open = (flags & DDM_OPEN) != 0;
-  const uint32_t packets = (q.nq + 31) / 32;
+  const uint32_t packets = (q.nq + (1u << q.qpp_log2) - 1u) >> q.qpp_log2;
   uint32_t blocks = (packets + kWarps - 1) / kWarps;
   const uint32_t cap = (uint32_t)sms * 8u;
   if (blocks > cap) blocks = cap;

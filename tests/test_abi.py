@@ -80,6 +80,7 @@ def test_every_call_refuses_a_null_context_without_gpu(lib):
     assert lib.ddm_set_replay_budget(None, 0) == A
     assert lib.ddm_set_tuning(None, 0, 8, 1) == A
     assert lib.ddm_set_update_id_base(None, 5) == A
+    assert lib.ddm_set_tiling(None, 32, 24) == A
     assert lib.ddm_debug_wait_timeout(None, 1, None) == A
     assert lib.ddm_batch_match(None, 1, 1, None, None, None, 0, None, None, None, 0, 0, None, 0,
                                None, ctypes.byref(k), None) == A
