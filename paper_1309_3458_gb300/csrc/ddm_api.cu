@@ -7,6 +7,8 @@
 #include <cstring>
 #include <new>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "ddm_internal.cuh"
 
 using namespace ddm;
@@ -99,6 +101,15 @@ struct ddm_ctx {
 };
 
 namespace {
+
+// NVTX range around a phase of a call (tree build, plan, write pass, refit),
+// so that a timeline tool shows the library's phases by name.  NVTX is
+// header-only and costs nothing when no tool is attached.
+class Phase {
+ public:
+  explicit Phase(const char* name) { nvtxRangePushA(name); }
+  ~Phase() { nvtxRangePop(); }
+};
 
 class DeviceGuard {
  public:
@@ -361,6 +372,7 @@ int order_set(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_t cnt,
 // no host synchronisation).
 int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t n, cudaStream_t s,
                 const BatchSet* bs = nullptr) {
+  Phase phase("ddm build");
   c->built = false;
   c->attached = false;
   c->swapped = false;
@@ -424,6 +436,7 @@ QueryView query_view(ddm_ctx* c) {
 // Validate U, sort it, count per update, scan (no host synchronisation).
 int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint32_t flags,
                bool record, cudaStream_t s, const BatchSet* bs = nullptr) {
+  Phase phase("ddm plan");
   c->planned = false;
   const int d = c->tree.d;
   DDM_TRY(ensure(c, c->counts, sizeof(uint32_t) * (m ? m : 1)));
@@ -530,6 +543,7 @@ bool base_fits(const ddm_ctx* c) { return (uint64_t)c->upd_base + c->m <= (1ull 
 
 int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint64_t capacity,
                 cudaStream_t s, const uint32_t* qids = nullptr) {
+  Phase phase("ddm write");
   if (!qids && !c->swapped && !c->bv.count && !base_fits(c)) return DDM_ERR_ARG;
   if (end > begin && c->tree.n > 0) {
     QueryView q = query_view(c);
@@ -569,6 +583,7 @@ int write_async(ddm_ctx* c, uint32_t begin, uint32_t end, ddm_pair* pairs, uint6
 // Write pass for the plan positions [pb, pe), laid out in plan order.
 int write_ordered_async(ddm_ctx* c, uint32_t pb, uint32_t pe, ddm_pair* pairs, uint64_t capacity,
                         cudaStream_t s, uint32_t* ids = nullptr) {
+  Phase phase("ddm write ordered");
   if (!ids && !base_fits(c)) return DDM_ERR_ARG;
   if (pe > pb && c->tree.n > 0) {
     QueryView q = query_view(c);
@@ -1073,6 +1088,7 @@ int ddm_refit(ddm_ctx* c, const float* sub_lo, const float* sub_hi, void* stream
   StreamUse use(c, s);
   DDM_TRY(reset_status(c, s));
   c->planned = false;
+  Phase phase("ddm refit");
   if (c->tree.n > 0) {
     float2* aos = aos_buffer(c, c->tree.d, c->tree.n);
     DDM_CUDA(launch_validate(c->tree.d, sub_lo, sub_hi, c->tree.n, nullptr, nullptr, 0, aos,
