@@ -402,9 +402,13 @@ int ddm_set_tuning(ddm_ctx *ctx, int str_shift, uint32_t ctas_per_sm, uint32_t r
  *                        (default 32; the leaves keep 32 subscriptions, one
  *                        per lane);
  *  swap_min           -- 1..33: a leaf met by at least this many of a
- *                        packet's queries is tested with the loops swapped
- *                        (lane = query, loop over the leaf's subscriptions);
- *                        33 = never (default 24).
+ *                        packet's queries is tested with lane = query: for
+ *                        d <= 3 from the leaf's rank tables (its bounds
+ *                        sorted per dimension, built with the tree), each
+ *                        lane finding its query's matches in the leaf by
+ *                        binary searches; for d > 3 by comparing the leaf's
+ *                        32 subscriptions one by one, from max(swap_min, 24)
+ *                        queries on.  33 = never (default 12).
  * Changing queries_per_packet drops the current plan (its records are laid
  * out by packet).  DDM_ERR_ARG outside these values or for a NULL context.
  * The paper has no counterpart (Section IV's queries run one per thread). */

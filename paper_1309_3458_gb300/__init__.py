@@ -437,7 +437,7 @@ def ddm_set_tuning(ctx: int, str_shift: int = 0, ctas_per_sm: int = 8, replay: i
     _check(lib().ddm_set_tuning(ctx, str_shift, ctas_per_sm, replay), "ddm_set_tuning")
 
 
-def ddm_set_tiling(ctx: int, queries_per_packet: int = 32, swap_min: int = 24) -> None:
+def ddm_set_tiling(ctx: int, queries_per_packet: int = 32, swap_min: int = 12) -> None:
     """Speed-only tiling of the query kernels: 16 or 32 queries per warp, and
     the number of a packet's queries on a leaf from which the count pass swaps
     its loops (33 = never).  Results never depend on it."""

@@ -21,11 +21,11 @@ from typing import Callable, Dict, Iterable, List, Optional, Tuple
 import paper_1309_3458_gb300 as ddm
 
 DEFAULT_SPACE = {"str_shift": (-1, 0, 1), "ctas_per_sm": (4, 8), "replay": (1, 0),
-                 "queries_per_packet": (32, 16), "swap_min": (16, 24, 33)}
+                 "queries_per_packet": (32, 16), "swap_min": (8, 12, 24)}
 TUNING = ("str_shift", "ctas_per_sm", "replay")
 TILING = ("queries_per_packet", "swap_min")
 DEFAULTS = {"str_shift": 0, "ctas_per_sm": 8, "replay": 1, "queries_per_packet": 32,
-            "swap_min": 24}
+            "swap_min": 12}
 
 
 def apply(ctx: int, cand: Dict[str, int]) -> None:

@@ -56,7 +56,8 @@ struct ddm_ctx {
   // sort scratch (shared by the subscription and the update sorts)
   DevBuf keys[2], vals[2], hist, lookback, counters;
   // tree
-  DevBuf e, sid, nodes;
+  DevBuf e, sid, nodes, tab;
+  bool tables_on = true;        // rank tables of the leaves (ddm_set_tiling)
   // plan: sorted updates, per-update counts and offsets
   DevBuf qe, qid, counts, counts_pos, offsets, pos_offsets, sums, work;
   // range selection for ddm_write over a sub-range of updates
@@ -86,7 +87,7 @@ struct ddm_ctx {
   // tiling (ddm_set_tiling): log2 of the queries per packet, and the number of
   // a packet's queries meeting a leaf from which the count pass swaps the loops
   uint32_t qpp_log2 = 5;
-  uint32_t tmin = 24;
+  uint32_t tmin = 12;
 
   bool built = false;
   bool attached = false;        // tree borrowed from another context (ddm_attach)
@@ -401,9 +402,15 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
   t.e = static_cast<const float2*>(c->e.p);
   t.sid = static_cast<const uint32_t*>(c->sid.p);
   t.nodes = static_cast<const float2*>(c->nodes.p);
+  // Rank tables of the leaves (d <= 3): 544 bytes per leaf and dimension.
+  // Optional: without room for them the swapped leaf test compares instead.
+  t.tab = nullptr;
+  if (d <= 3 && c->tables_on &&
+      ensure(c, c->tab, sizeof(uint32_t) * 2u * kRankSlot * (size_t)d * t.cnt[1]) == DDM_OK)
+    t.tab = static_cast<const uint32_t*>(c->tab.p);
   DDM_CUDA(launch_build(t, static_cast<const uint32_t*>(c->vals[cur].p), slo, shi, aos,
                         static_cast<float2*>(c->e.p), static_cast<uint32_t*>(c->sid.p),
-                        static_cast<float2*>(c->nodes.p), s));
+                        static_cast<float2*>(c->nodes.p), const_cast<uint32_t*>(t.tab), s));
   c->tree = t;
   c->built = true;
   return DDM_OK;
@@ -677,7 +684,7 @@ int ddm_destroy(ddm_ctx* c) {
   DeviceGuard g(c->device);
   cudaDeviceSynchronize();
   for (DevBuf* b : {&c->keys[0], &c->keys[1], &c->vals[0], &c->vals[1], &c->hist, &c->lookback,
-                    &c->counters, &c->e, &c->sid, &c->nodes, &c->qe, &c->qid, &c->counts,
+                    &c->counters, &c->e, &c->sid, &c->nodes, &c->tab, &c->qe, &c->qid, &c->counts,
                     &c->counts_pos, &c->offsets, &c->pos_offsets, &c->sums, &c->work,
                     &c->sel_offs, &c->sel_list, &c->rec, &c->blk_next, &c->blk_count,
                     &c->blk_pkt, &c->pkt_first, &c->pkt_nblk, &c->pkt_off,
@@ -1096,7 +1103,8 @@ int ddm_refit(ddm_ctx* c, const float* sub_lo, const float* sub_hi, void* stream
     // Same order, new coordinates: gather through the tree's own id column and
     // recompute every node's per-dimension (minlower, maxupper).
     DDM_CUDA(launch_build(c->tree, c->tree.sid, sub_lo, sub_hi, aos, static_cast<float2*>(c->e.p),
-                          static_cast<uint32_t*>(c->sid.p), static_cast<float2*>(c->nodes.p), s));
+                          static_cast<uint32_t*>(c->sid.p), static_cast<float2*>(c->nodes.p),
+                          const_cast<uint32_t*>(c->tree.tab), s));
   }
   DDM_TRY(sync_status(c, s));
   const int rc = status_code(*c->st_host);

@@ -45,7 +45,14 @@ struct TreeView {
   const float2* e;                // [d][n] (lo, hi) per dimension, sorted order
   const uint32_t* sid;            // [n] subscription id per sorted position
   const float2* nodes;            // [d][total] (minlower, maxupper) per dimension
+  // Rank tables (d <= 3, else null): per leaf g and slot 2k (lower bounds of
+  // dimension k) / 2k + 1 (upper bounds), kRankSlot words at
+  // (g * 2d + slot) * kRankSlot: the leaf's 32 bounds sorted ascending (float
+  // bits, padding positions +inf), then at word 35 + c the mask of the leaf
+  // positions holding the c smallest (c = 0..32).
+  const uint32_t* tab;
 };
+constexpr uint32_t kRankSlot = 68;  // words per rank-table slot (16-byte multiple)
 
 // Read-only view of the planned updates (queries) in their sorted order.
 struct QueryView {
@@ -184,7 +191,7 @@ void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* tota
 void str_groups(uint32_t n, int d, int* glog2, int shift = 0);
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
                          const float* hi, const float2* aos, float2* e, uint32_t* sid,
-                         float2* nodes, cudaStream_t s);
+                         float2* nodes, uint32_t* tab, cudaStream_t s);
 cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s);
 
 // ---- ddm_query.cu ---------------------------------------------------------

@@ -19,8 +19,14 @@
 //     box meets the leaf's box are tested one after the other: every lane
 //     holds one subscription and applies the segment test of Alg. 1 in every
 //     dimension (the reduction of Section III-A), and a ballot yields that
-//     query's matches in the leaf; when many of them meet the leaf, the loops
-//     swap (lane = query, loop over the leaf's subscriptions).
+//     query's matches in the leaf; when many of them meet the leaf, the
+//     roles swap (lane = query): for d <= 3 each lane finds its query's
+//     matches from the leaf's rank tables -- per dimension the leaf's lower
+//     and upper bounds sorted, with the mask of positions holding the c
+//     smallest -- by one binary search per bound, the same set as the
+//     segment tests since {lo_k <= q.hi_k} is a prefix of the sorted lower
+//     bounds and {hi_k >= q.lo_k} the complement of a prefix of the sorted
+//     upper bounds; for d > 3 by a loop over the leaf's subscriptions.
 //
 // The count pass adds up matches per update and leaves replay records; the
 // write pass (k_replay) expands the records into (update, subscription)
@@ -44,6 +50,10 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
+// Without rank tables (d > 3, or no room for them) the swapped leaf test
+// compares the leaf's 32 subscriptions one by one, which pays only from about
+// this many queries on a leaf.
+constexpr uint32_t kCompareSwapMin = 24;
 // Resident 256-thread blocks per SM the packet kernels are compiled for.
 #ifndef DDM_PACKET_MIN_BLOCKS
 #define DDM_PACKET_MIN_BLOCKS 4
@@ -175,6 +185,9 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
   __shared__ float4 s_q[kWarps][32][RW];
   __shared__ uint32_t s_list[WRITE ? 1 : kWarps][32];  // count pass: rows of a leaf's queries
   __shared__ float4 s_e[WRITE ? 1 : kWarps][32][DP];  // count pass: a leaf's subscriptions
+  // count pass, d <= 3: a leaf's rank tables (2d slots of kRankSlot words)
+  constexpr int TW = (!WRITE && D >= 1 && D <= 3) ? 2 * D * (int)kRankSlot : 4;
+  __shared__ __align__(16) uint32_t s_tab[kWarps][TW];
   __shared__ uint2 s_rng[kWarps][BATCH ? 32 : 1];  // per query: its instance's positions
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t lt = lanemask_lt();
@@ -289,53 +302,41 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
         if (!WRITE) ntests += __popc(qm);
         const uint32_t i = (g1 + cl) * 32u + lane;
         const bool iv = i < n;
-        float2 ev[DM];
-#pragma unroll
-        for (int k = 0; k < DM; ++k)
-          if (k < d) ev[k] = iv ? t.e[k * n + i] : make_float2(NAN, NAN);  // fails every test
-        uint32_t my_sid = 0;
-        if (WRITE && iv) my_sid = t.sid[i];
         uint32_t my_hb = 0;  // count pass: this lane's query's hit mask in the leaf
-        if (!WRITE && __popc(qm) >= q.tmin) {
-          // Swapped loops: stage the leaf's subscriptions, then every lane
-          // tests its own query against all 32 of them (the same segment
-          // tests of Alg. 1 in every dimension, in the opposite order).
+        bool by_rank = false;
+        if constexpr (!WRITE && D >= 1 && D <= 3) by_rank = t.tab && __popc(qm) >= q.tmin;
+        if (by_rank) {
+          // Rank tables (lane = query): per dimension k, the leaf positions
+          // with lo_k <= q.hi_k are those of the c smallest lower bounds, c
+          // found by a 6-step search in the sorted bounds; those with
+          // hi_k >= q.lo_k are all but the c' smallest upper bounds below
+          // q.lo_k.  The hit mask is their intersection over the dimensions:
+          // the segment test of Alg. 1 in every dimension (Section III-A),
+          // for all 32 subscriptions at once.
+          const float4* src = reinterpret_cast<const float4*>(
+              t.tab + (size_t)(g1 + cl) * (2u * D) * kRankSlot);
+          float4* dst = reinterpret_cast<float4*>(&s_tab[wib][0]);
+          constexpr int NV = 2 * D * (int)kRankSlot / 4;
 #pragma unroll
-          for (int k2 = 0; k2 < DP; ++k2) {
-            if (2 * k2 < d)
-              s_e[wib][lane][k2] = make_float4(ev[2 * k2].x, ev[2 * k2].y,
-                                               2 * k2 + 1 < d ? ev[2 * k2 + 1].x : 0.f,
-                                               2 * k2 + 1 < d ? ev[2 * k2 + 1].y : 0.f);
+          for (int j = lane; j < NV; j += 32) dst[j] = __ldg(src + j);
+          __syncwarp();
+          uint32_t hbm = __ballot_sync(0xffffffffu, iv);  // padding positions of the last leaf
+#pragma unroll
+          for (int k = 0; k < D; ++k) {
+            const uint32_t* sl = &s_tab[wib][2 * k * kRankSlot];
+            const uint32_t* sh = sl + kRankSlot;
+            const float xh = qh[k], xl = ql[k];
+            uint32_t c = 0u, c2 = 0u;
+#pragma unroll
+            for (int step = 16; step >= 1; step >>= 1) {
+              c += le<OPEN>(__uint_as_float(sl[c + step - 1]), xh) ? (uint32_t)step : 0u;
+              c2 += !le<OPEN>(xl, __uint_as_float(sh[c2 + step - 1])) ? (uint32_t)step : 0u;
+            }
+            c += le<OPEN>(__uint_as_float(sl[c]), xh) ? 1u : 0u;
+            c2 += !le<OPEN>(xl, __uint_as_float(sh[c2])) ? 1u : 0u;
+            hbm &= sl[35 + c] & ~sh[35 + c2];
           }
           __syncwarp();
-          uint32_t hbm = 0;
-          if constexpr (D >= 1 && D <= 3) {
-#pragma unroll
-            for (int e = 0; e < 32; ++e) {
-              const float4 b0 = s_e[wib][e][0], b1 = D == 3 ? s_e[wib][e][DP - 1] : b0;
-              if (OPEN)
-                seg_or_lt<D>(hbm, 1u << e, b0, b1, ql, qh);
-              else
-                seg_or_le<D>(hbm, 1u << e, b0, b1, ql, qh);
-            }
-          } else {  // runtime d (up to 8)
-#pragma unroll 8
-            for (int e = 0; e < 32; ++e) {
-              bool hit = true;
-#pragma unroll
-              for (int k2 = 0; k2 < DP; ++k2) {
-                if (2 * k2 < d) {
-                  const float4 b = s_e[wib][e][k2];
-                  hit = hit & le<OPEN>(b.x, qh[2 * k2]) & le<OPEN>(ql[2 * k2], b.y);
-                  if (2 * k2 + 1 < d)
-                    hit = hit & le<OPEN>(b.z, qh[2 * k2 + 1]) & le<OPEN>(ql[2 * k2 + 1], b.w);
-                }
-              }
-              hbm |= (hit ? 1u : 0u) << e;
-            }
-          }
-          __syncwarp();
-          hbm &= __ballot_sync(0xffffffffu, iv);  // padding lanes of the last leaf
           if (BATCH) {  // only this query's instance: positions [r_lo, r_hi)
             const uint32_t base = (g1 + cl) * 32u;
             const uint32_t a = r_lo > base ? min(r_lo - base, 32u) : 0u;
@@ -345,92 +346,149 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
             hbm &= upto_b & ~upto_a;
           }
           my_hb = ((qm >> lane) & 1u) ? hbm : 0u;
-          qm = 0u;
-        }
-        if (!WRITE && qm) {
-          // Queries of the leaf as a list of row offsets (in float4 units);
-          // two per iteration, each the segment tests of Alg. 1 in every
-          // dimension and one ballot, its hit mask stored into its row (every
-          // lane stores the same word).
-          const bool mine = (qm >> lane) & 1u;
-          const uint32_t nq = __popc(qm);
-          if (mine) s_list[wib][__popc(qm & lt)] = (uint32_t)(lane * RW);
-          __syncwarp();
-          const float4* rows = &s_q[wib][0][0];
-          uint32_t* hbw = reinterpret_cast<uint32_t*>(&s_q[wib][0][0]);
-          auto test = [&](uint32_t r) {
-            if constexpr (D >= 1 && D <= 3 && !BATCH) {
-              const float4 b0 = rows[r], b1 = D == 3 ? rows[r + 1] : b0;
-              hbw[4 * r + HB] = OPEN ? seg_ballot_lt<D>(ev, b0, b1) : seg_ballot_le<D>(ev, b0, b1);
-              return;
+        } else {
+          float2 ev[DM];
+  #pragma unroll
+          for (int k = 0; k < DM; ++k)
+            if (k < d) ev[k] = iv ? t.e[k * n + i] : make_float2(NAN, NAN);  // fails every test
+          uint32_t my_sid = 0;
+          if (WRITE && iv) my_sid = t.sid[i];
+          if (!WRITE && __popc(qm) >= max(q.tmin, kCompareSwapMin)) {
+            // Swapped loops: stage the leaf's subscriptions, then every lane
+            // tests its own query against all 32 of them (the same segment
+            // tests of Alg. 1 in every dimension, in the opposite order).
+  #pragma unroll
+            for (int k2 = 0; k2 < DP; ++k2) {
+              if (2 * k2 < d)
+                s_e[wib][lane][k2] = make_float4(ev[2 * k2].x, ev[2 * k2].y,
+                                                 2 * k2 + 1 < d ? ev[2 * k2 + 1].x : 0.f,
+                                                 2 * k2 + 1 < d ? ev[2 * k2 + 1].y : 0.f);
             }
+            __syncwarp();
+            uint32_t hbm = 0;
+            if constexpr (D >= 1 && D <= 3) {
+  #pragma unroll
+              for (int e = 0; e < 32; ++e) {
+                const float4 b0 = s_e[wib][e][0], b1 = D == 3 ? s_e[wib][e][DP - 1] : b0;
+                if (OPEN)
+                  seg_or_lt<D>(hbm, 1u << e, b0, b1, ql, qh);
+                else
+                  seg_or_le<D>(hbm, 1u << e, b0, b1, ql, qh);
+              }
+            } else {  // runtime d (up to 8)
+  #pragma unroll 8
+              for (int e = 0; e < 32; ++e) {
+                bool hit = true;
+  #pragma unroll
+                for (int k2 = 0; k2 < DP; ++k2) {
+                  if (2 * k2 < d) {
+                    const float4 b = s_e[wib][e][k2];
+                    hit = hit & le<OPEN>(b.x, qh[2 * k2]) & le<OPEN>(ql[2 * k2], b.y);
+                    if (2 * k2 + 1 < d)
+                      hit = hit & le<OPEN>(b.z, qh[2 * k2 + 1]) & le<OPEN>(ql[2 * k2 + 1], b.w);
+                  }
+                }
+                hbm |= (hit ? 1u : 0u) << e;
+              }
+            }
+            __syncwarp();
+            hbm &= __ballot_sync(0xffffffffu, iv);  // padding lanes of the last leaf
+            if (BATCH) {  // only this query's instance: positions [r_lo, r_hi)
+              const uint32_t base = (g1 + cl) * 32u;
+              const uint32_t a = r_lo > base ? min(r_lo - base, 32u) : 0u;
+              const uint32_t b = r_hi > base ? min(r_hi - base, 32u) : 0u;
+              const uint32_t upto_b = b >= 32u ? 0xffffffffu : ((1u << b) - 1u);
+              const uint32_t upto_a = a >= 32u ? 0xffffffffu : ((1u << a) - 1u);
+              hbm &= upto_b & ~upto_a;
+            }
+            my_hb = ((qm >> lane) & 1u) ? hbm : 0u;
+            qm = 0u;
+          }
+          if (!WRITE && qm) {
+            // Queries of the leaf as a list of row offsets (in float4 units);
+            // two per iteration, each the segment tests of Alg. 1 in every
+            // dimension and one ballot, its hit mask stored into its row (every
+            // lane stores the same word).
+            const bool mine = (qm >> lane) & 1u;
+            const uint32_t nq = __popc(qm);
+            if (mine) s_list[wib][__popc(qm & lt)] = (uint32_t)(lane * RW);
+            __syncwarp();
+            const float4* rows = &s_q[wib][0][0];
+            uint32_t* hbw = reinterpret_cast<uint32_t*>(&s_q[wib][0][0]);
+            auto test = [&](uint32_t r) {
+              if constexpr (D >= 1 && D <= 3 && !BATCH) {
+                const float4 b0 = rows[r], b1 = D == 3 ? rows[r + 1] : b0;
+                hbw[4 * r + HB] = OPEN ? seg_ballot_lt<D>(ev, b0, b1) : seg_ballot_le<D>(ev, b0, b1);
+                return;
+              }
+              bool hit = iv;
+              if (BATCH) {
+                const uint2 rg = s_rng[wib][r / RW];
+                hit = hit & (i >= rg.x) & (i < rg.y);
+              }
+  #pragma unroll
+              for (int k2 = 0; k2 < DP; ++k2) {
+                if (2 * k2 < d) {
+                  const float4 b = rows[r + k2];
+                  hit = hit & le<OPEN>(ev[2 * k2].x, b.y) & le<OPEN>(b.x, ev[2 * k2].y);
+                  if (2 * k2 + 1 < d)
+                    hit = hit & le<OPEN>(ev[2 * k2 + 1].x, b.w) & le<OPEN>(b.z, ev[2 * k2 + 1].y);
+                }
+              }
+              hbw[4 * r + HB] = __ballot_sync(0xffffffffu, hit);
+            };
+            uint32_t j = 0;
+            for (; j + 2u <= nq; j += 2u) {
+              const uint2 rr = *reinterpret_cast<const uint2*>(&s_list[wib][j]);
+              test(rr.x);
+              test(rr.y);
+            }
+            if (j < nq) test(s_list[wib][j]);
+            __syncwarp();
+            my_hb = mine ? hbw[4 * lane * RW + HB] : 0u;
+            qm = 0u;
+          }
+          while (qm) {
+            const int qq = __ffs(qm) - 1;
+            qm &= qm - 1u;
             bool hit = iv;
+            uint32_t sub_base = 0;
             if (BATCH) {
-              const uint2 rg = s_rng[wib][r / RW];
+              const uint2 rg = s_rng[wib][qq];
               hit = hit & (i >= rg.x) & (i < rg.y);
+              sub_base = rg.x;
             }
-#pragma unroll
+  #pragma unroll
             for (int k2 = 0; k2 < DP; ++k2) {
               if (2 * k2 < d) {
-                const float4 b = rows[r + k2];
+                const float4 b = s_q[wib][qq][k2];
                 hit = hit & le<OPEN>(ev[2 * k2].x, b.y) & le<OPEN>(b.x, ev[2 * k2].y);
                 if (2 * k2 + 1 < d)
                   hit = hit & le<OPEN>(ev[2 * k2 + 1].x, b.w) & le<OPEN>(b.z, ev[2 * k2 + 1].y);
               }
             }
-            hbw[4 * r + HB] = __ballot_sync(0xffffffffu, hit);
-          };
-          uint32_t j = 0;
-          for (; j + 2u <= nq; j += 2u) {
-            const uint2 rr = *reinterpret_cast<const uint2*>(&s_list[wib][j]);
-            test(rr.x);
-            test(rr.y);
-          }
-          if (j < nq) test(s_list[wib][j]);
-          __syncwarp();
-          my_hb = mine ? hbw[4 * lane * RW + HB] : 0u;
-          qm = 0u;
-        }
-        while (qm) {
-          const int qq = __ffs(qm) - 1;
-          qm &= qm - 1u;
-          bool hit = iv;
-          uint32_t sub_base = 0;
-          if (BATCH) {
-            const uint2 rg = s_rng[wib][qq];
-            hit = hit & (i >= rg.x) & (i < rg.y);
-            sub_base = rg.x;
-          }
-#pragma unroll
-          for (int k2 = 0; k2 < DP; ++k2) {
-            if (2 * k2 < d) {
-              const float4 b = s_q[wib][qq][k2];
-              hit = hit & le<OPEN>(ev[2 * k2].x, b.y) & le<OPEN>(b.x, ev[2 * k2].y);
-              if (2 * k2 + 1 < d)
-                hit = hit & le<OPEN>(ev[2 * k2 + 1].x, b.w) & le<OPEN>(b.z, ev[2 * k2 + 1].y);
-            }
-          }
-          const uint32_t hb = __ballot_sync(0xffffffffu, hit);
-          if (WRITE) {
-            const unsigned long long o = __shfl_sync(0xffffffffu, out, qq);
-            const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
-            if (hit) {
-              const unsigned long long at = o + __popc(hb & lt);
-              if (at < w.capacity) {
-                if (w.ids) {
-                  w.ids[at] = my_sid - sub_base;
-                } else {
-                  ddm_pair pr;
-                  pr.upd = Qq;
-                  pr.sub = my_sid - sub_base;
-                  if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
-                  w.pairs[at] = pr;
+            const uint32_t hb = __ballot_sync(0xffffffffu, hit);
+            if (WRITE) {
+              const unsigned long long o = __shfl_sync(0xffffffffu, out, qq);
+              const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
+              if (hit) {
+                const unsigned long long at = o + __popc(hb & lt);
+                if (at < w.capacity) {
+                  if (w.ids) {
+                    w.ids[at] = my_sid - sub_base;
+                  } else {
+                    ddm_pair pr;
+                    pr.upd = Qq;
+                    pr.sub = my_sid - sub_base;
+                    if (w.swap) pr = ddm_pair{pr.sub, pr.upd};
+                    w.pairs[at] = pr;
+                  }
                 }
               }
+              if (lane == qq) out = o + __popc(hb);
+            } else {
+              if (lane == qq) my_hb = hb;
             }
-            if (lane == qq) out = o + __popc(hb);
-          } else {
-            if (lane == qq) my_hb = hb;
           }
         }
         if (recording) {

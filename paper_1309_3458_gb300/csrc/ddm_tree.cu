@@ -37,13 +37,48 @@ __device__ __forceinline__ float warp_min(float v) {
   return v;
 }
 
+// Sorts the warp's 32 keys ascending (bitonic network over shuffles; ties by
+// lane) and writes them and their prefix masks into one rank-table slot of
+// kRankSlot words: slot[j] = the j-th smallest key, slot[35 + c] = the bits
+// of the lanes holding the c smallest keys (c = 0..32; words 32..35 are 0).
+__device__ __forceinline__ void rank_slot(float key, int lane, uint32_t* __restrict__ slot) {
+  uint32_t idx = (uint32_t)lane;
+#pragma unroll
+  for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      const float ok = __shfl_xor_sync(0xffffffffu, key, j);
+      const uint32_t oi = __shfl_xor_sync(0xffffffffu, idx, j);
+      const bool mine_less = key < ok || (key == ok && idx < oi);
+      const bool keep_min = ((lane & j) == 0) == ((lane & k) == 0);
+      if (keep_min != mine_less) {
+        key = ok;
+        idx = oi;
+      }
+    }
+  }
+  uint32_t m = 1u << idx;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, m, o);
+    if (lane >= o) m |= y;
+  }
+  slot[lane] = __float_as_uint(key);
+  slot[36 + lane] = m;
+  if (lane < 4) slot[32 + lane] = 0u;
+}
+
 // Gather the sorted SoA layout and build levels 1 and 2.  One CTA of 1024
 // threads covers 1024 sorted positions: one warp per level-1 node, and the
-// CTA's 32 level-1 nodes form level-2 node blockIdx.x.
+// CTA's 32 level-1 nodes form level-2 node blockIdx.x.  With `tab` (d <= 3)
+// it also writes every leaf's rank tables: per dimension k, its 32 lower
+// bounds (slot 2k) and 32 upper bounds (slot 2k + 1) sorted, with prefix
+// masks, padding positions holding +inf.
 __global__ void __launch_bounds__(1024)
 k_gather_build(TreeView t, const uint32_t* __restrict__ sorted_ids, const float* __restrict__ lo,
                const float* __restrict__ hi, const float2* __restrict__ aos,
-               float2* __restrict__ e, uint32_t* __restrict__ sid, float2* __restrict__ nodes) {
+               float2* __restrict__ e, uint32_t* __restrict__ sid, float2* __restrict__ nodes,
+               uint32_t* __restrict__ tab) {
   __shared__ float s_min[DDM_MAX_DIMS][32], s_max[DDM_MAX_DIMS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t n = t.n;
@@ -71,6 +106,11 @@ k_gather_build(TreeView t, const uint32_t* __restrict__ sorted_ids, const float*
     }
     const float mn = warp_min(valid ? a : INFINITY);
     const float mx = warp_max(valid ? b : -INFINITY);
+    if (tab && gvalid) {  // warp-uniform
+      uint32_t* slot = tab + ((size_t)g * 2u * (uint32_t)t.d + 2u * (uint32_t)k) * kRankSlot;
+      rank_slot(valid ? a : INFINITY, lane, slot);
+      rank_slot(valid ? b : INFINITY, lane, slot + kRankSlot);
+    }
     if (lane == 0) {
       if (gvalid) nodes[(size_t)k * t.total + t.off[1] + g] = make_float2(mn, mx);
       s_min[k][w] = gvalid ? mn : INFINITY;
@@ -150,10 +190,10 @@ void str_groups(uint32_t n, int d, int* glog2, int shift) {
 
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
                          const float* hi, const float2* aos, float2* e, uint32_t* sid,
-                         float2* nodes, cudaStream_t s) {
+                         float2* nodes, uint32_t* tab, cudaStream_t s) {
   if (t.n == 0) return cudaSuccess;
   const uint32_t blocks = (t.n + 1023) / 1024;
-  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, aos, e, sid, nodes);
+  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, aos, e, sid, nodes, tab);
   if (t.L >= 3) k_build_upper<<<1, 1024, 0, s>>>(t, nodes);
   note_launches(t.L >= 3 ? 2u : 1u);
   return cudaGetLastError();

@@ -126,3 +126,34 @@ def test_autotuned_batched_workload_against_oracle(ctx):
         _, ou, os_ = oracle.itm_pairs(*a)
         assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(ou, os_))), (i, best)
     AT.apply(ctx, {})
+
+
+@pytest.mark.parametrize("qpp,swap_min", [(32, 1), (16, 1), (32, 33), (32, 12)])
+@pytest.mark.parametrize("flags", [0, 1])
+def test_leaf_test_forms_exact_against_oracle(ctx, qpp, swap_min, flags):
+    """Every leaf visit through one form: swap_min 1 sends all of them
+    through the rank tables (d <= 3), 33 through the per-query comparisons;
+    tie-heavy grids, signed zeros, infinite bounds, degenerate and identical
+    extents, ragged leaves -- pair sets equal to the oracle's."""
+    from tests.test_gpu_parity import check_exact
+    ddm.ddm_set_tiling(ctx, qpp, swap_min)
+    try:
+        for d in (1, 2, 3):
+            for seed in range(6):
+                rng = np.random.default_rng(77 + seed)
+                n, m = (int(v) for v in rng.integers(1, 400, size=2))
+                arrays = W.grid_random(n, m, d, seed=seed, grid=5)
+                if seed == 5:   # infinite bounds in the mix
+                    arrays[3][0, :3] = np.inf
+                    arrays[2][d - 1, :2] = -np.inf
+                    arrays[0][0, :2] = -np.inf
+                check_exact(ctx, arrays, flags)
+        lo = np.array([[-0.0, 0.0, -np.inf, 5.0, 5.0, 5.0, 1e30, -1e-30] * 5], np.float32)
+        hi = np.array([[0.0, 0.0, np.inf, 5.0, 5.0, 6.0, np.inf, 0.0] * 5], np.float32)
+        check_exact(ctx, (lo.copy(), hi.copy(), lo.copy(), hi.copy()), flags)
+        same = (np.full((3, 700), 7.0, np.float32), np.full((3, 700), 9.0, np.float32))
+        check_exact(ctx, (same[0][:, :90].copy(), same[1][:, :90].copy(), same[0], same[1]), flags)
+        for n, m in ((33, 64), (1025, 300), (4097, 97)):
+            check_exact(ctx, W.uniform_fixed_length(n, m, 3, 0.2 * (n + m), seed=n), flags)
+    finally:
+        AT.apply(ctx, {})
