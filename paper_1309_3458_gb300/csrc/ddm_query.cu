@@ -684,10 +684,17 @@ constexpr int kOutPairs = 0, kOutSwapped = 1, kOutIds = 2;
 // or four records per group, was slower.  Subscription ids (4-byte stores)
 // go the other way: four CTAs with eight records take 122.3 ms, three 138.0,
 // two 178.7.
+//
+// The ids form also expands differently (dense): per round of 32 records, a
+// scan of their hit counts turns the hit bits into a list of pairs, and each
+// lane then writes one id of the list (one load and one 32-lane store per 32
+// ids) -- 115.1 instead of 122.1 ms; for pairs that form is slower (147.6 at
+// three CTAs, 168.8 at two).
 template <int OUT>
 struct ReplayShape {
   static constexpr int ctas = OUT == 2 ? 4 : 2;
   static constexpr int group = OUT == 2 ? 8 : 16;
+  static constexpr bool dense = OUT == 2;
 };
 template <bool FILTER_ID, bool WIDE, bool BATCH, int OUT>
 __global__ void __launch_bounds__(kThreads, ReplayShape<OUT>::ctas)
@@ -700,6 +707,10 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
   // the subscription id base, the position then in s_at.
   __shared__ uint4 s_rec[kWarps][32];
   __shared__ Cursor s_at[kWarps][32];
+  constexpr bool kDense = ReplayShape<OUT>::dense;
+  // dense expansion: each round's pairs as a list of (record, leaf slot)
+  __shared__ uint32_t s_pre[kDense ? kWarps : 1][32];
+  __shared__ uint16_t s_list[kDense ? kWarps : 1][kDense ? 1024 : 2];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const uint32_t below = (1u << lane) - 1u;  // lanes below this one
   const uint32_t lanebit = 1u << lane;
@@ -769,6 +780,48 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
       constexpr bool kPacked = !WIDE && !BATCH;  // position fits the record's fourth word
       s_rec[wib][lane] = make_uint4(x >> 5, hb, Qq, kPacked ? (uint32_t)o : sb);
       if (!kPacked) s_at[wib][lane] = o;
+      if constexpr (kDense) {
+        // The round's pairs, numbered record by record: an exclusive scan of
+        // the records' hit counts gives each record's first pair; the hit
+        // bits become a list of (record, leaf slot) in that numbering
+        // (lane = leaf slot); then every lane takes one pair of the list at
+        // a time: one id load and one store per 32 pairs.
+        const uint32_t c = __popc(hb);
+        uint32_t incl = c;
+#pragma unroll
+        for (int dd = 1; dd < 32; dd <<= 1) {
+          const uint32_t v = __shfl_up_sync(0xffffffffu, incl, dd);
+          if (lane >= dd) incl += v;
+        }
+        const uint32_t total = __shfl_sync(0xffffffffu, incl, 31);
+        s_pre[wib][lane] = incl - c;
+        __syncwarp();
+#pragma unroll 8
+        for (int u = 0; u < 32; ++u) {
+          const uint32_t h = s_rec[wib][u].y;
+          if (h & lanebit)
+            s_list[wib][s_pre[wib][u] + __popc(h & below)] = (uint16_t)(((uint32_t)u << 5) | (uint32_t)lane);
+        }
+        __syncwarp();
+#pragma unroll 2
+        for (uint32_t t = lane; t < total; t += 32u) {
+          const uint32_t ent = s_list[wib][t];
+          const uint32_t r = ent >> 5, slot = ent & 31u;
+          const uint4 R = s_rec[wib][r];
+          const uint32_t sv = ld_hinted(sid + R.x * 32u + slot, keep);
+          const Cursor at = (kPacked ? (Cursor)R.w : s_at[wib][r]) + (Cursor)(t - s_pre[wib][r]);
+          const uint32_t sub = sv - (kPacked ? 0u : R.w);
+          if (OUT == kOutIds) {
+            st_hinted(ids + (unsigned long long)at, sub, stream);
+          } else {
+            ddm_pair pr;
+            pr.upd = OUT == kOutSwapped ? sub : R.z;
+            pr.sub = OUT == kOutSwapped ? R.z : sub;
+            st_hinted(pairs + (unsigned long long)at, pr, stream);
+          }
+        }
+        continue;
+      }
       __syncwarp();
 #pragma unroll 1
       constexpr int G = ReplayShape<OUT>::group;
