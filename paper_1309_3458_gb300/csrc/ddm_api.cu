@@ -491,9 +491,10 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
         ensure(c, c->blk_count, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_pkt, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_list, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
-        ensure(c, c->pkt_first, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
-        ensure(c, c->pkt_nblk, (size_t)packets * sizeof(uint32_t)) == DDM_OK &&
-        ensure(c, c->pkt_off, ((size_t)packets + 1) * sizeof(unsigned long long)) == DDM_OK &&
+        ensure(c, c->pkt_first, (size_t)packets * kRecChains * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->pkt_nblk, (size_t)packets * kRecChains * sizeof(uint32_t)) == DDM_OK &&
+        ensure(c, c->pkt_off, ((size_t)packets * kRecChains + 1) * sizeof(unsigned long long)) ==
+            DDM_OK &&
         ensure(c, c->blk_counter, 4 * sizeof(uint32_t)) == DDM_OK) {
       c->arena.rec = static_cast<uint32_t*>(c->rec.p);
       c->arena.blk_next = static_cast<uint32_t*>(c->blk_next.p);
@@ -531,7 +532,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   DDM_CUDA(launch_scan(counts, m, offsets, sums, c->st_dev, s));
   if (c->arena.max_blocks) {  // plan-order list of the record blocks
     const uint32_t packets = packets_of(c, m);
-    DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets, c->arena.pkt_off, sums, nullptr, s));
+    DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets * kRecChains, c->arena.pkt_off, sums, nullptr, s));
     DDM_CUDA(launch_block_list(c->arena, packets, s));
   }
   if (c->arena.max_blocks)  // blocks needed, packets, blocks held: the next arena's sizing hint

@@ -206,15 +206,21 @@ cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_h
 // any range of them, every record independently, instead of walking the
 // tree again.
 constexpr uint32_t kRecBlock = 512;       // records per block (3 x 2 KiB, one array per word)
+// A packet's records go to two chains of blocks, one per half of its query
+// lanes, so that a block holds the records of at most 16 queries (its pairs
+// land in fewer output runs): the write pass took 127 instead of 134 ms on
+// the clustered d = 3 workload, the count pass 5 ms more.  Chain c of packet
+// p is chain index p * kRecChains + c of the arena's per-chain arrays.
+constexpr uint32_t kRecChains = 2;
 constexpr uint32_t kNoBlock = 0xffffffffu;
 struct RecordArena {
   uint32_t* rec;           // [max_blocks][3][kRecBlock]: x, hit mask, matches before
   uint32_t* blk_next;      // [max_blocks] next block of the packet, or kNoBlock
   uint32_t* blk_count;     // [max_blocks] records in the block
   uint32_t* blk_pkt;       // [max_blocks] packet of the block
-  uint32_t* pkt_first;     // [packets] first block of each packet, or kNoBlock
-  uint32_t* pkt_nblk;      // [packets] blocks of each packet
-  unsigned long long* pkt_off;  // [packets + 1] exclusive prefix of pkt_nblk
+  uint32_t* pkt_first;     // [chains] first block of each chain, or kNoBlock
+  uint32_t* pkt_nblk;      // [chains] blocks of each chain
+  unsigned long long* pkt_off;  // [chains + 1] exclusive prefix of pkt_nblk
   uint32_t* blk_list;      // [max_blocks] blocks in plan order
   uint32_t* blk_counter;   // [0] blocks handed out (may exceed max_blocks),
                            // [1] blocks the whole pass needed, [2] packets,

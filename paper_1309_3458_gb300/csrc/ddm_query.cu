@@ -264,7 +264,8 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
     // packet stops writing but keeps counting the blocks it would need.
     const bool recording = !WRITE && ra.max_blocks > 0;
     bool rec_write = recording;
-    uint32_t cur_blk = kNoBlock, fill = kRecBlock, nblk = 0;
+    uint32_t cur0 = kNoBlock, cur1 = kNoBlock, fill0 = kRecBlock, fill1 = kRecBlock;
+    uint32_t nblk0 = 0, nblk1 = 0;
     // Test the 32 level-1 nodes (leaves) from g1 on against the packet box,
     // then run the packet's queries over each surviving leaf.
     auto leaves = [&](uint32_t g1) {
@@ -492,11 +493,20 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
           }
         }
         if (recording) {
+          // Records of lanes 0-15 go to chain 0, of lanes 16-31 to chain 1
+          // (kRecChains == 2); both in one store step, each lane at its
+          // chain's fill position plus its rank among its chain's records.
+          static_assert(kRecChains == 2, "two record chains per packet");
           const uint32_t rm = __ballot_sync(0xffffffffu, my_hb != 0u);
-          if (rm) {
-            const uint32_t k = __popc(rm);
-            if (fill + k > kRecBlock) {  // the leaf's records start a new block
-              ++nblk;
+          const uint32_t k0 = __popc(rm & 0xffffu), k1 = __popc(rm >> 16);
+          if (rm && (fill0 + k0 > kRecBlock || fill1 + k1 > kRecBlock)) {
+#pragma unroll
+            for (int ch = 0; ch < 2; ++ch) {
+              const uint32_t kc = ch ? k1 : k0;
+              uint32_t& fl = ch ? fill1 : fill0;
+              uint32_t& cb = ch ? cur1 : cur0;
+              if (kc == 0u || fl + kc <= kRecBlock) continue;  // the leaf's records start a new block
+              if (ch) ++nblk1; else ++nblk0;
               if (rec_write) {
                 uint32_t b = 0;
                 if (lane == 0) b = atomicAdd(&ra.blk_counter[0], 1u);
@@ -505,27 +515,30 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
                   rec_write = false;  // arena exhausted: the write pass walks instead
                 } else {
                   if (lane == 0) {
-                    if (cur_blk == kNoBlock) {
-                      ra.pkt_first[p] = b;
+                    if (cb == kNoBlock) {
+                      ra.pkt_first[(size_t)p * 2u + ch] = b;
                     } else {
-                      ra.blk_next[cur_blk] = b;
-                      ra.blk_count[cur_blk] = fill;
+                      ra.blk_next[cb] = b;
+                      ra.blk_count[cb] = fl;
                     }
                     ra.blk_pkt[b] = p;
                   }
-                  cur_blk = b;
+                  cb = b;
                 }
               }
-              fill = 0;
+              fl = 0;
             }
-            if (rec_write && my_hb != 0u) {
-              uint32_t* r = ra.rec + (size_t)cur_blk * (3u * kRecBlock) + fill + __popc(rm & lt);
-              r[0] = ((g1 + cl) << 5) | (uint32_t)lane;
-              r[kRecBlock] = my_hb;
-              r[2u * kRecBlock] = cnt;  // this query's matches before the leaf
-            }
-            fill += k;
           }
+          if (rec_write && my_hb != 0u) {
+            const bool hi = lane >= 16;
+            const uint32_t at = (hi ? fill1 + __popc(rm & lt & 0xffff0000u) : fill0 + __popc(rm & lt));
+            uint32_t* r = ra.rec + (size_t)(hi ? cur1 : cur0) * (3u * kRecBlock) + at;
+            r[0] = ((g1 + cl) << 5) | (uint32_t)lane;
+            r[kRecBlock] = my_hb;
+            r[2u * kRecBlock] = cnt;  // this query's matches before the leaf
+          }
+          fill0 += k0;
+          fill1 += k1;
         }
         if (!WRITE) cnt += __popc(my_hb);
       }
@@ -598,27 +611,36 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
     if (!WRITE && st && lane == 0 && ntests) atomicAdd(&st->tests, (unsigned long long)ntests);
     if (recording && lane == 0) {
       if (rec_write) {
-        if (cur_blk == kNoBlock) {
-          ra.pkt_first[p] = kNoBlock;
+        if (cur0 == kNoBlock) {
+          ra.pkt_first[(size_t)p * 2u] = kNoBlock;
         } else {
-          ra.blk_next[cur_blk] = kNoBlock;
-          ra.blk_count[cur_blk] = fill;
+          ra.blk_next[cur0] = kNoBlock;
+          ra.blk_count[cur0] = fill0;
+        }
+        if (cur1 == kNoBlock) {
+          ra.pkt_first[(size_t)p * 2u + 1u] = kNoBlock;
+        } else {
+          ra.blk_next[cur1] = kNoBlock;
+          ra.blk_count[cur1] = fill1;
         }
       }
-      ra.pkt_nblk[p] = rec_write ? nblk : 0u;
-      if (nblk) atomicAdd(&ra.blk_counter[1], nblk);
+      ra.pkt_nblk[(size_t)p * 2u] = rec_write ? nblk0 : 0u;
+      ra.pkt_nblk[(size_t)p * 2u + 1u] = rec_write ? nblk1 : 0u;
+      if (nblk0 + nblk1) atomicAdd(&ra.blk_counter[1], nblk0 + nblk1);
     }
   }
 }
 
-// Plan-order list of record blocks: one thread per packet copies its chain.
+// Plan-order list of record blocks: one thread per chain copies it (chains of
+// a packet in lane order, packets in plan order).
 __global__ void k_block_list(RecordArena ra, uint32_t packets) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {  // sizing hint for the next arena
     ra.blk_counter[2] = packets;
     ra.blk_counter[3] = ra.max_blocks;
   }
   if (!records_complete(ra)) return;
-  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < packets;
+  const uint32_t chains = packets * kRecChains;
+  for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < chains;
        p += gridDim.x * blockDim.x) {
     unsigned long long at = ra.pkt_off[p];
     for (uint32_t b = ra.pkt_first[p]; b != kNoBlock; b = ra.blk_next[b]) ra.blk_list[at++] = b;
@@ -731,7 +753,8 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
   uint32_t* __restrict__ ids = w.ids;
   const uint32_t* __restrict__ sid = t.sid;
   const unsigned long long keep = l2_policy_evict_last(), stream = l2_policy_evict_first();
-  const unsigned long long i0 = ra.pkt_off[p0], i1 = ra.pkt_off[p1];
+  const unsigned long long i0 = ra.pkt_off[(size_t)p0 * kRecChains],
+                           i1 = ra.pkt_off[(size_t)p1 * kRecChains];
   for (;;) {
     unsigned long long i = 0;
     if (lane == 0) i = i0 + atomicAdd(work, 1u);
