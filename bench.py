@@ -42,9 +42,11 @@ sys.path.insert(0, ROOT)
 DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
 # DRAM bytes (read + write) per pair of the write-pass kernel (k_replay), from
 # the ncu capture summarised in profiles/k_replay_clustered_d3_scale0.15.md
-# (a smaller case of the same workload; traffic scales with pairs written).
-# None until a capture of the current kernel exists.
-TRAFFIC_PER_PAIR = None
+# (a smaller case of the same workload; traffic scales with pairs written),
+# and per id of the compressed output's kernel
+# (profiles/k_replay_ids_clustered_d3_scale0.15.md).
+TRAFFIC_PER_PAIR = 8.86
+TRAFFIC_PER_ID = 5.49
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
@@ -803,6 +805,7 @@ def main():
             "roofline": {"bound": "hbm", "kernel": "k_replay (ddm_write_ordered_ids)",
                          "achieved": c_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": c_gbs / hbm_peak, "peak_source": peak_src,
+                         "traffic": TRAFFIC_PER_ID * sum(cw_ids) / max(1, len(cw_ids)),
                          "bytes_per_launch": "4*(ids in chunk): each id written once"}}
 
     # ---- end to end with host buffers ----
