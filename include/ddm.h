@@ -67,6 +67,8 @@ extern "C" {
 #define DDM_ERR_CUDA      5  /* a CUDA runtime call or kernel launch failed */
 #define DDM_ERR_TIMEOUT   6  /* a bounded device-side wait gave up */
 #define DDM_ERR_STATE     7  /* staged call without the build / plan it needs */
+#define DDM_ERR_INTERNAL  8  /* checked build (libddm_checked.so) only: a kernel found an
+                                index outside its bounds and skipped the access */
 
 /* Flags. */
 #define DDM_CLOSED 0u  /* default: closed segments, x.lo <= y.hi && y.lo <= x.hi */

@@ -19,7 +19,10 @@ import os
 from typing import Optional, Sequence, Tuple
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libddm.so")
+# DDM_LIBRARY=checked selects the checked build (kernels verify their indices
+# and report DDM_ERR_INTERNAL instead of touching memory out of bounds).
+LIB_PATH = os.path.join(HERE, "libddm_checked.so" if os.environ.get("DDM_LIBRARY") == "checked"
+                        else "libddm.so")
 
 DDM_OK = 0
 DDM_ERR_ARG = 1
@@ -29,6 +32,7 @@ DDM_ERR_NOMEM = 4
 DDM_ERR_CUDA = 5
 DDM_ERR_TIMEOUT = 6
 DDM_ERR_STATE = 7
+DDM_ERR_INTERNAL = 8
 
 DDM_CLOSED = 0
 DDM_OPEN = 1
@@ -104,7 +108,8 @@ def lib():
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(f"{LIB_PATH} missing: build it with "
-                               "`python -m paper_1309_3458_gb300.build`")
+                               "`python -m paper_1309_3458_gb300.build`"
+                               + (" --checked" if LIB_PATH.endswith("_checked.so") else ""))
         L = ctypes.CDLL(LIB_PATH)
         for name, (res, args) in SIGNATURES.items():
             f = getattr(L, name)

@@ -5,7 +5,13 @@ file under ``_build/``; the objects are linked into
 ``paper_1309_3458_gb300/libddm.so`` with the CUDA runtime linked statically,
 so the library loads on any machine with the driver alone.
 
-Run ``python -m paper_1309_3458_gb300.build`` (or call ``build()``).
+``build(checked=True)`` builds the checked variant instead,
+``libddm_checked.so`` (objects under ``_build_checked/``, compiled with
+``DDM_CHECKED``): its kernels verify the indices they use and report an index
+out of bounds as ``DDM_ERR_INTERNAL`` instead of touching memory.  The
+binding loads it when ``DDM_LIBRARY=checked`` is set.
+
+Run ``python -m paper_1309_3458_gb300.build [--checked]`` (or call ``build()``).
 """
 from __future__ import annotations
 
@@ -21,6 +27,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddm.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libddm_checked.so")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -44,36 +52,42 @@ def headers():
     return hs
 
 
-def _compile(src: str, extra) -> str:
-    obj = os.path.join(BUILD, os.path.basename(src) + ".o")
+def _compile(src: str, flags, build_dir: str, force: bool) -> str:
+    """Compile one translation unit unless its object is newer than the source
+    and every header (or `force`)."""
+    obj = os.path.join(build_dir, os.path.basename(src) + ".o")
     newest_dep = max([os.path.getmtime(src)] + [os.path.getmtime(h) for h in headers()])
-    if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not extra:
+    if os.path.exists(obj) and os.path.getmtime(obj) >= newest_dep and not force:
         return obj
-    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(extra) + ["-c", src, "-o", obj]
+    cmd = [nvcc()] + ARCH + NVCC_FLAGS + list(flags) + ["-c", src, "-o", obj]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
     return obj
 
 
-def build(verbose: bool = False, extra=()) -> str:
-    """Compile every ``csrc/*.cu`` and link ``libddm.so``; returns its path."""
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, extra=(), checked: bool = False) -> str:
+    """Compile every ``csrc/*.cu`` and link ``libddm.so`` (or, with
+    ``checked``, ``libddm_checked.so``); returns its path."""
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    flags = list(extra) + (["-DDDM_CHECKED"] if checked else [])
+    os.makedirs(build_dir, exist_ok=True)
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, extra), srcs))
-    if (not os.path.exists(LIB) or extra
-            or os.path.getmtime(LIB) < max(os.path.getmtime(o) for o in objs)):
-        tmp = LIB + f".tmp{os.getpid()}"
+        objs = list(ex.map(lambda s: _compile(s, flags, build_dir, bool(extra)), srcs))
+    if (not os.path.exists(lib) or extra
+            or os.path.getmtime(lib) < max(os.path.getmtime(o) for o in objs)):
+        tmp = lib + f".tmp{os.getpid()}"
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", tmp] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-        os.replace(tmp, LIB)
+        os.replace(tmp, lib)
     if verbose:
-        print(LIB)
-    return LIB
+        print(lib)
+    return lib
 
 
 if __name__ == "__main__":
-    build(verbose=True, extra=sys.argv[1:])
+    args = [a for a in sys.argv[1:] if a != "--checked"]
+    build(verbose=True, extra=args, checked="--checked" in sys.argv[1:])

@@ -225,6 +225,7 @@ int sync_status(ddm_ctx* c, cudaStream_t s) {
 }
 
 int status_code(const Status& st) {
+  if (st.err & kErrChecked) return DDM_ERR_INTERNAL;
   if (st.err & kErrTimeout) return DDM_ERR_TIMEOUT;
   if (st.err & kErrExtent) return DDM_ERR_EXTENT;
   if (st.err & kErrCapacity) return DDM_ERR_CAPACITY;
@@ -410,7 +411,8 @@ int build_async(ddm_ctx* c, int d, const float* slo, const float* shi, uint32_t 
     t.tab = static_cast<const uint32_t*>(c->tab.p);
   DDM_CUDA(launch_build(t, static_cast<const uint32_t*>(c->vals[cur].p), slo, shi, aos,
                         static_cast<float2*>(c->e.p), static_cast<uint32_t*>(c->sid.p),
-                        static_cast<float2*>(c->nodes.p), const_cast<uint32_t*>(t.tab), s));
+                        static_cast<float2*>(c->nodes.p), const_cast<uint32_t*>(t.tab),
+                        c->st_dev, s));
   c->tree = t;
   c->built = true;
   return DDM_OK;
@@ -636,6 +638,7 @@ const char* ddm_strerror(int code) {
     case DDM_ERR_CUDA: return "CUDA error";
     case DDM_ERR_TIMEOUT: return "bounded device wait timed out";
     case DDM_ERR_STATE: return "tree or plan missing";
+    case DDM_ERR_INTERNAL: return "an index failed its bounds check (checked build)";
     default: return "unknown error";
   }
 }
@@ -1105,7 +1108,7 @@ int ddm_refit(ddm_ctx* c, const float* sub_lo, const float* sub_hi, void* stream
     // recompute every node's per-dimension (minlower, maxupper).
     DDM_CUDA(launch_build(c->tree, c->tree.sid, sub_lo, sub_hi, aos, static_cast<float2*>(c->e.p),
                           static_cast<uint32_t*>(c->sid.p), static_cast<float2*>(c->nodes.p),
-                          const_cast<uint32_t*>(c->tree.tab), s));
+                          const_cast<uint32_t*>(c->tree.tab), c->st_dev, s));
   }
   DDM_TRY(sync_status(c, s));
   const int rc = status_code(*c->st_host);

@@ -20,6 +20,7 @@ constexpr int kMaxLevels = DDM_MAX_TREE_LEVELS;
 constexpr unsigned kErrExtent = 1u;
 constexpr unsigned kErrTimeout = 2u;
 constexpr unsigned kErrCapacity = 4u;
+constexpr unsigned kErrChecked = 8u;  // checked build: an index failed its bounds check
 
 // Device-resident status word read back once per synchronising call.
 struct Status {
@@ -29,6 +30,24 @@ struct Status {
   unsigned long long aux;  // call-specific (chunk end, ...)
   unsigned long long tests;  // count pass: (query, leaf) tests, 32 subscriptions each
 };
+
+__device__ inline void note_out_of_bounds(Status* st) {
+  if (st) atomicOr(&st->err, kErrChecked);
+}
+
+// Checked build (compiled with DDM_CHECKED, as libddm_checked.so): kernels
+// verify the indices they are about to use, and an index out of its bounds
+// sets kErrChecked in the status word (the call returns DDM_ERR_INTERNAL)
+// and the access is skipped -- never a trap.  In the normal build the check
+// is the constant true and costs nothing.
+#ifdef DDM_CHECKED
+#define DDM_IN_BOUNDS(cond, st) ((cond) ? true : (::ddm::note_out_of_bounds(st), false))
+#else
+#define DDM_IN_BOUNDS(cond, st) true
+#endif
+
+struct Status;
+__device__ inline void note_out_of_bounds(Status* st);
 
 // Read-only view of a built tree, passed to kernels by value.
 //
@@ -191,7 +210,7 @@ void tree_shape(uint32_t n, int* L, uint32_t* cnt, uint32_t* off, uint32_t* tota
 void str_groups(uint32_t n, int d, int* glog2, int shift = 0);
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
                          const float* hi, const float2* aos, float2* e, uint32_t* sid,
-                         float2* nodes, uint32_t* tab, cudaStream_t s);
+                         float2* nodes, uint32_t* tab, Status* st, cudaStream_t s);
 cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_hi, cudaStream_t s);
 
 // ---- ddm_query.cu ---------------------------------------------------------

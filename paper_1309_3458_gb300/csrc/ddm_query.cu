@@ -532,10 +532,12 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
           if (rec_write && my_hb != 0u) {
             const bool hi = lane >= 16;
             const uint32_t at = (hi ? fill1 + __popc(rm & lt & 0xffff0000u) : fill0 + __popc(rm & lt));
-            uint32_t* r = ra.rec + (size_t)(hi ? cur1 : cur0) * (3u * kRecBlock) + at;
-            r[0] = ((g1 + cl) << 5) | (uint32_t)lane;
-            r[kRecBlock] = my_hb;
-            r[2u * kRecBlock] = cnt;  // this query's matches before the leaf
+            if (DDM_IN_BOUNDS(at < kRecBlock && (hi ? cur1 : cur0) < ra.max_blocks, st)) {
+              uint32_t* r = ra.rec + (size_t)(hi ? cur1 : cur0) * (3u * kRecBlock) + at;
+              r[0] = ((g1 + cl) << 5) | (uint32_t)lane;
+              r[kRecBlock] = my_hb;
+              r[2u * kRecBlock] = cnt;  // this query's matches before the leaf
+            }
           }
           fill0 += k0;
           fill1 += k1;
@@ -604,7 +606,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
         }
       }
     }
-    if (!WRITE && valid) {
+    if (!WRITE && valid && DDM_IN_BOUNDS(Q < m, st)) {
       counts[Q] = cnt;
       if (counts_pos) counts_pos[pos] = cnt;
     }
@@ -827,12 +829,13 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
         }
         __syncwarp();
 #pragma unroll 2
-        for (uint32_t t = lane; t < total; t += 32u) {
-          const uint32_t ent = s_list[wib][t];
+        for (uint32_t ti = lane; ti < total; ti += 32u) {
+          const uint32_t ent = s_list[wib][ti];
           const uint32_t r = ent >> 5, slot = ent & 31u;
           const uint4 R = s_rec[wib][r];
+          const Cursor at = (kPacked ? (Cursor)R.w : s_at[wib][r]) + (Cursor)(ti - s_pre[wib][r]);
+          if (!DDM_IN_BOUNDS(R.x * 32u + slot < t.n && (unsigned long long)at < need, st)) continue;
           const uint32_t sv = ld_hinted(sid + R.x * 32u + slot, keep);
-          const Cursor at = (kPacked ? (Cursor)R.w : s_at[wib][r]) + (Cursor)(t - s_pre[wib][r]);
           const uint32_t sub = sv - (kPacked ? 0u : R.w);
           if (OUT == kOutIds) {
             st_hinted(ids + (unsigned long long)at, sub, stream);
@@ -855,13 +858,15 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
         for (int u = 0; u < G; ++u) {
           rr[u] = s_rec[wib][g + u];
           sv[u] = 0u;
-          if (rr[u].y & lanebit) sv[u] = ld_hinted(sid + rr[u].x * 32u + (uint32_t)lane, keep);
+          if ((rr[u].y & lanebit) && DDM_IN_BOUNDS(rr[u].x * 32u + (uint32_t)lane < t.n, st))
+            sv[u] = ld_hinted(sid + rr[u].x * 32u + (uint32_t)lane, keep);
         }
 #pragma unroll
         for (int u = 0; u < G; ++u) {
           if (rr[u].y & lanebit) {
             const Cursor at = kPacked ? (Cursor)rr[u].w : s_at[wib][g + u];
             const unsigned long long slot = (unsigned long long)(at + (Cursor)__popc(rr[u].y & below));
+            if (!DDM_IN_BOUNDS(slot < need, st)) continue;
             const uint32_t sub = sv[u] - (kPacked ? 0u : rr[u].w);
             if (OUT == kOutIds) {
               st_hinted(ids + slot, sub, stream);

@@ -230,8 +230,10 @@ k_onesweep(const unsigned long long* __restrict__ in_keys, const uint32_t* __res
   for (uint32_t s = tid; s < tile_valid; s += kThreads) {
     const unsigned long long k = sm.keys[s];
     const uint32_t g = sm.gbase[(uint32_t)(k >> shift) & (kRadix - 1)] + s;
-    out_keys[g] = k;
-    out_vals[g] = sm.vals[s];
+    if (DDM_IN_BOUNDS(g < n, st)) {
+      out_keys[g] = k;
+      out_vals[g] = sm.vals[s];
+    }
   }
 }
 

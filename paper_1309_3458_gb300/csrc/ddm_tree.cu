@@ -78,15 +78,18 @@ __global__ void __launch_bounds__(1024)
 k_gather_build(TreeView t, const uint32_t* __restrict__ sorted_ids, const float* __restrict__ lo,
                const float* __restrict__ hi, const float2* __restrict__ aos,
                float2* __restrict__ e, uint32_t* __restrict__ sid, float2* __restrict__ nodes,
-               uint32_t* __restrict__ tab) {
+               uint32_t* __restrict__ tab, Status* __restrict__ st) {
   __shared__ float s_min[DDM_MAX_DIMS][32], s_max[DDM_MAX_DIMS][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const uint32_t n = t.n;
   const uint32_t i = blockIdx.x * 1024u + threadIdx.x;
   const bool valid = i < n;
   uint32_t id = 0;
+  bool valid_id = valid;
   if (valid) {
     id = sorted_ids[i];
+    valid_id = DDM_IN_BOUNDS(id < n, st);
+    if (!valid_id) id = 0;
     sid[i] = id;
   }
   const uint32_t g = blockIdx.x * 32u + w;
@@ -190,10 +193,10 @@ void str_groups(uint32_t n, int d, int* glog2, int shift) {
 
 cudaError_t launch_build(const TreeView& t, const uint32_t* sorted_ids, const float* lo,
                          const float* hi, const float2* aos, float2* e, uint32_t* sid,
-                         float2* nodes, uint32_t* tab, cudaStream_t s) {
+                         float2* nodes, uint32_t* tab, Status* st, cudaStream_t s) {
   if (t.n == 0) return cudaSuccess;
   const uint32_t blocks = (t.n + 1023) / 1024;
-  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, aos, e, sid, nodes, tab);
+  k_gather_build<<<blocks, 1024, 0, s>>>(t, sorted_ids, lo, hi, aos, e, sid, nodes, tab, st);
   if (t.L >= 3) k_build_upper<<<1, 1024, 0, s>>>(t, nodes);
   note_launches(t.L >= 3 ? 2u : 1u);
   return cudaGetLastError();

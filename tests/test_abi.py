@@ -37,7 +37,7 @@ def test_every_symbol_exported(lib):
 
 
 def test_strerror(lib):
-    for code in range(8):
+    for code in range(9):
         assert ddm.ddm_strerror(code)
     assert ddm.ddm_strerror(99) == "unknown error"
 
@@ -223,3 +223,14 @@ def test_binding_rejects_counts_the_c_abi_cannot_carry(monkeypatch):
     huge = _FakeCuda((1, ddm.DDM_MAX_EXTENTS + 1), torch.float32, 0)
     with pytest.raises(ValueError, match="at most"):
         ddm.ddm_build(0x5151, huge, huge)
+
+
+def test_checked_build_exports_every_symbol():
+    """The bounds-checking variant (libddm_checked.so) builds and exports the
+    same entry points (no GPU needed)."""
+    path = B.build(checked=True)
+    L = ctypes.CDLL(path)
+    for name in declared():
+        assert hasattr(L, name), name
+    L.ddm_strerror.restype = ctypes.c_char_p
+    assert b"bounds" in L.ddm_strerror(ddm.DDM_ERR_INTERNAL)
