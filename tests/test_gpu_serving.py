@@ -211,3 +211,84 @@ def test_serving_scale_requests_exact():
         srv.close()
         ddm.ddm_destroy(ctx)
         regions.close()
+
+
+def test_adaptive_refit_policy_rebuilds_and_stays_exact():
+    """Refit every step with a probe-triggered rebuild: regions moving by
+    their own side per step age the order fast, so the probe finds the
+    refitted tree slower than the threshold and the version is rebuilt; every
+    request's pairs still equal its pinned version's, alone."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    d, n, l = 2, 40000, 3000.0
+    g = torch.Generator(device="cuda")
+    g.manual_seed(21)
+    lo = (torch.rand((d, n), generator=g, device="cuda") * (S.L - l)).contiguous()
+    hi = (lo + l).contiguous()
+    regions = S.ResidentRegions(lo, hi, keep_history=True, rebuild_every=0, adaptive=1.2)
+    state = {"lo": lo, "hi": hi}
+    mg = torch.Generator(device="cuda")
+    mg.manual_seed(5)
+
+    def mover(step):
+        state["lo"], state["hi"] = S.random_walk(state["lo"], state["hi"], 3000.0, mg)
+        return state["lo"], state["hi"]
+
+    sched = S.poisson_schedule(rate=8000.0, duration=0.02, federates=8, size_lo=500,
+                               size_hi=50000, seed=9)
+    srv = S.Server(regions, l, slots=2, pair_capacity=1 << 22, keep_pairs=True)
+    try:
+        done = srv.run(sched, mover=mover, step_s=0.002)
+    finally:
+        srv.close()
+    assert regions.refits >= 1 and regions.rebuilds >= 1
+    assert regions.tests_ratio and max(regions.tests_ratio) > 1.2
+    ctx = ddm.ddm_create(0)
+    try:
+        for r in done[::3]:
+            plo, phi = regions.history[r.step]
+            ulo, uhi = S.request_updates(r.seed, r.size, d, l)
+            K = ddm.ddm_count(ctx, ulo, uhi, plo, phi)
+            assert K == r.K
+            buf = torch.empty((max(K, 1), 2), dtype=torch.int32, device="cuda")
+            ddm.ddm_match(ctx, ulo, uhi, plo, phi, buf)
+            alone = buf[:K].cpu().numpy().view(np.uint32)
+            assert np.array_equal(np.sort(keys(r.pairs[:, 0], r.pairs[:, 1])),
+                                  np.sort(keys(alone[:, 0], alone[:, 1])))
+    finally:
+        ddm.ddm_destroy(ctx)
+        regions.close()
+
+
+def test_context_used_from_two_streams_with_workspace_growth():
+    """A context's calls may come on different streams: each call waits for
+    the context's previous one, so workspace grown (and freed in stream order)
+    on one stream never overlaps work still running on the other."""
+    import torch
+    from paper_1309_3458_gb300 import workloads as W
+    small = W.uniform_fixed_length(20000, 5000, 2, 10.0, seed=3)
+    big = W.uniform_fixed_length(20000, 400000, 2, 30.0, seed=4)
+    ctx = ddm.ddm_create(0)
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    try:
+        S_ = [torch.from_numpy(x).cuda() for x in small[2:]]
+        Us = [torch.from_numpy(x).cuda() for x in small[:2]]
+        Ub = [torch.from_numpy(x).cuda() for x in big[:2]]
+        torch.cuda.synchronize()
+        for rep in range(3):
+            with torch.cuda.stream(s1):
+                ddm.ddm_build(ctx, *S_, stream=s1)
+                ddm.ddm_plan_async(ctx, *Us, stream=s1)
+            with torch.cuda.stream(s2):      # larger plan: the workspace grows on s2
+                kb = ddm.ddm_plan(ctx, *Ub, stream=s2)
+                buf = torch.empty((kb, 2), dtype=torch.int32, device="cuda")
+                assert ddm.ddm_write(ctx, 0, big[0].shape[1], buf, stream=s2) == kb
+            torch.cuda.synchronize()
+            got = buf.cpu().numpy().view(np.uint32)
+            Ko, ou, os_ = oracle.itm_pairs(big[0], big[1], small[2], small[3])
+            assert kb == Ko
+            assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(ou, os_)))
+            del buf
+    finally:
+        ddm.ddm_destroy(ctx)
