@@ -219,7 +219,7 @@ cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_h
 // query lane, hit mask over the leaf's 32 subscriptions, and the query's
 // matches before this leaf (so the record knows where its pairs go in the
 // query's output).  Records of a packet are kept in walk order (leaf by
-// leaf, query lanes ascending within a leaf), in a chain of fixed-size
+// leaf, query lanes ascending within a leaf), in chains of fixed-size
 // blocks taken from a shared arena; a block stores its packet.  After
 // counting, the blocks are listed in plan order and the write pass expands
 // any range of them, every record independently, instead of walking the
@@ -234,13 +234,13 @@ constexpr uint32_t kRecChains = 2;
 constexpr uint32_t kNoBlock = 0xffffffffu;
 struct RecordArena {
   uint32_t* rec;           // [max_blocks][3][kRecBlock]: x, hit mask, matches before
-  uint32_t* blk_next;      // [max_blocks] next block of the packet, or kNoBlock
+  uint32_t* blk_next;      // [max_blocks] next block of the chain, or kNoBlock
   uint32_t* blk_count;     // [max_blocks] records in the block
   uint32_t* blk_pkt;       // [max_blocks] packet of the block
   uint32_t* pkt_first;     // [chains] first block of each chain, or kNoBlock
   uint32_t* pkt_nblk;      // [chains] blocks of each chain
   unsigned long long* pkt_off;  // [chains + 1] exclusive prefix of pkt_nblk
-  uint32_t* blk_list;      // [max_blocks] blocks in plan order
+  uint32_t* blk_list;      // [max_blocks] blocks in plan order (packet, then chain)
   uint32_t* blk_counter;   // [0] blocks handed out (may exceed max_blocks),
                            // [1] blocks the whole pass needed, [2] packets,
                            // [3] max_blocks (the last two for arena sizing)
@@ -266,8 +266,9 @@ cudaError_t launch_count(const TreeView& t, const QueryView& q, const BatchView&
 cudaError_t launch_write(const TreeView& t, const QueryView& q, const BatchView& bv,
                          uint32_t flags, const WriteView& w, const RecordArena& ra,
                          uint32_t* work, Status* st, int sms, cudaStream_t s);
-// After the count pass: blk_list = every packet's chain, packets in plan
-// order (pkt_off must already hold the prefix of pkt_nblk).
+// After the count pass: blk_list = every chain's blocks, chains in order
+// (packets in plan order, a packet's two chains in lane order); pkt_off must
+// already hold the prefix of pkt_nblk.
 cudaError_t launch_block_list(const RecordArena& ra, uint32_t packets, cudaStream_t s);
 // Write pass from records: packets [p0, p1) of the plan, positions [pb, pe),
 // and (when id_filter) only updates with ids in [idb, ide).  Does nothing
