@@ -221,27 +221,58 @@ def cpu_oracle_sample(arrays, budget_s, one_core: bool = False):
     return out
 
 
-def cpu_small_configs():
+def cpu_small_configs(reps: int = 30):
     """The oracle on the N = 1e4, d = 1 workload: brute force (Alg. 2) on one
     thread and the interval tree (Algs. 4-5, build included) on one thread
-    and on all host cores."""
+    and on all host cores, each the mean of `reps` runs (the paper reports
+    the mean of 30)."""
     import numpy as np
 
     import oracle
     from paper_1309_3458_gb300 import workloads as W
     a = W.make("uniform_d1_N1e4_a1")
     threads = len(os.sched_getaffinity(0))
-    out = {"workload": "uniform_d1_N1e4_a1"}
-    t0 = time.perf_counter()
-    K = oracle.bf(*a, pairs=False)[0]
-    out["bf_1core_s"] = time.perf_counter() - t0
-    for name, th in (("itm_1core_s", 1), ("itm_all_cores_s", threads)):
+    out = {"workload": "uniform_d1_N1e4_a1", "runs": reps}
+    ts = []
+    for _ in range(reps):
         t0 = time.perf_counter()
-        Ki, _, _ = oracle.itm_count(*a, threads=th)
-        out[name] = time.perf_counter() - t0
-        assert Ki == K
+        K = oracle.bf(*a, pairs=False)[0]
+        ts.append(time.perf_counter() - t0)
+    out["bf_1core_s"] = float(np.mean(ts))
+    for name, th in (("itm_1core_s", 1), ("itm_all_cores_s", threads)):
+        ts = []
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            Ki, _, _ = oracle.itm_count(*a, threads=th)
+            ts.append(time.perf_counter() - t0)
+            assert Ki == K
+        out[name] = float(np.mean(ts))
     out["K"] = int(K)
     out["cores"] = threads
+    return out
+
+
+def cpu_config2(budget_s: float = 2.0):
+    """The oracle's interval tree (Algs. 4-5) on the N = 1e6 workloads (d = 1
+    and 2, alpha = 0.01, 1, 100) on all host cores and on one: one build
+    over all subscriptions plus a sample of the updates sized to about
+    `budget_s`, the rate extrapolated to all updates (cpu_oracle_sample);
+    match_s is the extrapolated time of the whole matching, build included.
+    Brute force is not timed here: 2.5e11 segment tests per workload."""
+    from paper_1309_3458_gb300 import workloads as W
+    out = []
+    for d in (1, 2):
+        for tag in ("0.01", "1", "100"):
+            name = f"uniform_d{d}_N1e6_a{tag}"
+            a = W.make(name)
+            m = a[0].shape[1]
+            r = cpu_oracle_sample(a, budget_s, one_core=True)
+            out.append({"workload": name, "cores": r["cores"],
+                        "match_s_all_cores": m / r["queries_per_s"],
+                        "match_s_one_core": m / r["one_core"]["queries_per_s"],
+                        "pairs_per_s_all_cores": r["value"],
+                        "pairs_per_s_one_core": r["one_core"]["value"],
+                        "sample": r["sample"] + "; " + r["one_core"]["sample"]})
     return out
 
 
@@ -933,6 +964,7 @@ def main():
         cpu = cpu_oracle_sample(arrays, args.cpu_seconds, one_core=True)
         cpu.pop("seconds", None)
         cpu["small_configs"] = cpu_small_configs()
+        cpu["config2"] = cpu_config2()
 
     clocks = clk.summary()
     n_sms = torch.cuda.get_device_properties(local).multi_processor_count
