@@ -452,7 +452,10 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   DDM_TRY(ensure(c, c->counts_pos, sizeof(uint32_t) * (m ? m : 1)));
   DDM_TRY(ensure(c, c->offsets, sizeof(unsigned long long) * ((size_t)m + 1)));
   DDM_TRY(ensure(c, c->pos_offsets, sizeof(unsigned long long) * ((size_t)m + 1)));
-  DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * ((size_t)m / kScanTile + 2)));
+  // tile sums of the three scans below, one region each
+  const size_t upd_tiles = (size_t)m / kScanTile + 1;
+  const size_t blk_tiles = (size_t)packets_of(c, m) * kRecChains / kScanTile + 1;
+  DDM_TRY(ensure(c, c->sums, sizeof(unsigned long long) * (2 * upd_tiles + blk_tiles + 1)));
   DDM_TRY(ensure(c, c->work, sizeof(uint32_t)));
   DDM_TRY(ensure(c, c->qe, sizeof(float2) * (size_t)d * (m ? m : 1)));
   DDM_TRY(ensure(c, c->qid, sizeof(uint32_t) * (m ? m : 1)));
@@ -529,14 +532,17 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
       DDM_CUDA(cudaMemsetAsync(counts_pos, 0, sizeof(uint32_t) * m, s));
     }
   }
+  // offsets by plan position and by update id, and the record blocks' plan
+  // order, in one launch sequence
   auto* sums = static_cast<unsigned long long*>(c->sums.p);
-  DDM_CUDA(launch_scan(counts_pos, m, pos_offsets, sums, nullptr, s));
-  DDM_CUDA(launch_scan(counts, m, offsets, sums, c->st_dev, s));
-  if (c->arena.max_blocks) {  // plan-order list of the record blocks
-    const uint32_t packets = packets_of(c, m);
-    DDM_CUDA(launch_scan(c->arena.pkt_nblk, packets * kRecChains, c->arena.pkt_off, sums, nullptr, s));
-    DDM_CUDA(launch_block_list(c->arena, packets, s));
-  }
+  ScanJob jobs[kMaxScanJobs] = {{counts_pos, m, pos_offsets, sums, nullptr},
+                                {counts, m, offsets, sums + upd_tiles, c->st_dev}};
+  int njobs = 2;
+  if (c->arena.max_blocks)
+    jobs[njobs++] = ScanJob{c->arena.pkt_nblk, packets_of(c, m) * kRecChains, c->arena.pkt_off,
+                            sums + 2 * upd_tiles, nullptr};
+  DDM_CUDA(launch_scan_multi(jobs, njobs, s));
+  if (c->arena.max_blocks) DDM_CUDA(launch_block_list(c->arena, packets_of(c, m), s));
   if (c->arena.max_blocks)  // blocks needed, packets, blocks held: the next arena's sizing hint
     DDM_CUDA(cudaMemcpyAsync((void*)c->rec_hint, static_cast<uint32_t*>(c->blk_counter.p) + 1,
                              3 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));

@@ -287,6 +287,18 @@ constexpr int kScanTile = 4096;
 // offsets[0..m] = exclusive prefix of counts; offsets[m] and st->K = total.
 cudaError_t launch_scan(const uint32_t* counts, uint32_t m, unsigned long long* offsets,
                         unsigned long long* block_sums, Status* st, cudaStream_t s);
+// Up to kMaxScanJobs independent scans of the form above in one launch
+// sequence (three launches, or one when every job has m <= kScanTile).
+// Each job's `sums` needs max(1, ceil(m / kScanTile)) entries of its own.
+struct ScanJob {
+  const uint32_t* counts;
+  uint32_t m;
+  unsigned long long* offsets;
+  unsigned long long* sums;
+  Status* st;
+};
+constexpr int kMaxScanJobs = 3;
+cudaError_t launch_scan_multi(const ScanJob* jobs, int count, cudaStream_t s);
 cudaError_t launch_chunk_end(const unsigned long long* offsets, uint32_t m, uint32_t begin,
                              unsigned long long capacity, Status* st, cudaStream_t s);
 // list = sorted positions i (ascending) with begin <= qid[i] < end; uses

@@ -44,9 +44,10 @@ __device__ unsigned long long block_excl_scan(unsigned long long v, unsigned lon
   return pre + incl - v;
 }
 
-__global__ void __launch_bounds__(kThreads)
-k_tile_sums(const uint32_t* __restrict__ counts, uint32_t m, unsigned long long* __restrict__ sums) {
-  const size_t base = (size_t)blockIdx.x * kScanTile;
+// Sum of tile `tile` of counts into sums[tile].
+__device__ __forceinline__ void tile_sum(const uint32_t* __restrict__ counts, uint32_t m,
+                                         uint32_t tile, unsigned long long* __restrict__ sums) {
+  const size_t base = (size_t)tile * kScanTile;
   unsigned long long s = 0;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
@@ -55,13 +56,13 @@ k_tile_sums(const uint32_t* __restrict__ counts, uint32_t m, unsigned long long*
   }
   unsigned long long tot;
   block_excl_scan(s, &tot);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+  if (threadIdx.x == 0) sums[tile] = tot;
 }
 
 // One CTA: exclusive scan of the tile sums in place; total -> offsets[m], st->K.
-__global__ void __launch_bounds__(kThreads)
-k_scan_sums(unsigned long long* __restrict__ sums, uint32_t tiles, unsigned long long* __restrict__ offsets,
-            uint32_t m, Status* __restrict__ st) {
+__device__ __forceinline__ void scan_sums(unsigned long long* __restrict__ sums, uint32_t tiles,
+                                          unsigned long long* __restrict__ offsets, uint32_t m,
+                                          Status* __restrict__ st) {
   unsigned long long carry = 0;
   for (uint32_t c = 0; c < tiles; c += kThreads) {
     const uint32_t idx = c + threadIdx.x;
@@ -77,14 +78,17 @@ k_scan_sums(unsigned long long* __restrict__ sums, uint32_t tiles, unsigned long
   }
 }
 
-// ONE: a single tile (m <= kScanTile) scanned by one CTA with no tile sums;
-// it also writes the total to offsets[m] and st->K.
+// Offsets of tile `tile` from its scanned tile sum.  ONE: a single tile
+// (m <= kScanTile) with no tile sums, which also writes the total to
+// offsets[m] and st->K.
 template <bool ONE>
-__global__ void __launch_bounds__(kThreads)
-k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned long long* __restrict__ sums,
-             unsigned long long* __restrict__ offsets, Status* __restrict__ st) {
+__device__ __forceinline__ void scan_tile(const uint32_t* __restrict__ counts, uint32_t m,
+                                          uint32_t tile,
+                                          const unsigned long long* __restrict__ sums,
+                                          unsigned long long* __restrict__ offsets,
+                                          Status* __restrict__ st) {
   __shared__ uint32_t s_c[kScanTile];
-  const size_t base = (size_t)blockIdx.x * kScanTile;
+  const size_t base = (size_t)tile * kScanTile;
 #pragma unroll
   for (int i = 0; i < kItems; ++i) {
     const size_t idx = base + (size_t)i * kThreads + threadIdx.x;
@@ -96,7 +100,7 @@ k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned lon
 #pragma unroll
   for (int i = 0; i < kItems; ++i) local += s_c[threadIdx.x * kItems + i];
   unsigned long long tot;
-  unsigned long long run = (ONE ? 0ull : sums[blockIdx.x]) + block_excl_scan(local, &tot);
+  unsigned long long run = (ONE ? 0ull : sums[tile]) + block_excl_scan(local, &tot);
   if (ONE && threadIdx.x == 0) {
     offsets[m] = tot;
     if (st) st->K = tot;
@@ -124,6 +128,57 @@ k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned lon
     }
     __syncthreads();
   }
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_tile_sums(const uint32_t* __restrict__ counts, uint32_t m, unsigned long long* __restrict__ sums) {
+  tile_sum(counts, m, blockIdx.x, sums);
+}
+
+__global__ void __launch_bounds__(kThreads)
+k_scan_sums(unsigned long long* __restrict__ sums, uint32_t tiles, unsigned long long* __restrict__ offsets,
+            uint32_t m, Status* __restrict__ st) {
+  scan_sums(sums, tiles, offsets, m, st);
+}
+
+template <bool ONE>
+__global__ void __launch_bounds__(kThreads)
+k_scan_tiles(const uint32_t* __restrict__ counts, uint32_t m, const unsigned long long* __restrict__ sums,
+             unsigned long long* __restrict__ offsets, Status* __restrict__ st) {
+  scan_tile<ONE>(counts, m, blockIdx.x, sums, offsets, st);
+}
+
+// Several independent scans in the same three launches: the CTAs of the
+// per-tile kernels are numbered over the jobs' tiles one job after another
+// (job j owns CTAs [tile0[j], tile0[j + 1])); the tile-sum scan runs one
+// CTA per job.  ONE: every job is a single tile, one launch in all.
+struct ScanJobs {
+  ScanJob job[kMaxScanJobs];
+  uint32_t tile0[kMaxScanJobs + 1];
+  int count;
+};
+
+__device__ __forceinline__ int job_of(const ScanJobs& js, uint32_t cta) {
+  int j = 0;
+  while (j + 1 < js.count && cta >= js.tile0[j + 1]) ++j;
+  return j;
+}
+
+__global__ void __launch_bounds__(kThreads) k_tile_sums_multi(const ScanJobs js) {
+  const int j = job_of(js, blockIdx.x);
+  tile_sum(js.job[j].counts, js.job[j].m, blockIdx.x - js.tile0[j], js.job[j].sums);
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_sums_multi(const ScanJobs js) {
+  const ScanJob& jb = js.job[blockIdx.x];
+  scan_sums(jb.sums, js.tile0[blockIdx.x + 1] - js.tile0[blockIdx.x], jb.offsets, jb.m, jb.st);
+}
+
+template <bool ONE>
+__global__ void __launch_bounds__(kThreads) k_scan_tiles_multi(const ScanJobs js) {
+  const int j = job_of(js, blockIdx.x);
+  const ScanJob& jb = js.job[j];
+  scan_tile<ONE>(jb.counts, jb.m, blockIdx.x - js.tile0[j], jb.sums, jb.offsets, jb.st);
 }
 
 // Largest e in [begin, m] with offsets[e] - offsets[begin] <= capacity.
@@ -183,6 +238,31 @@ cudaError_t launch_scan(const uint32_t* counts, uint32_t m, unsigned long long* 
   if (tiles > 0)
     k_scan_tiles<false><<<tiles, kThreads, 0, s>>>(counts, m, block_sums, offsets, nullptr);
   note_launches(tiles > 0 ? 3u : 1u);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scan_multi(const ScanJob* jobs, int count, cudaStream_t s) {
+  if (count < 1 || count > kMaxScanJobs) return cudaErrorInvalidValue;
+  ScanJobs js = {};
+  js.count = count;
+  bool one = true;
+  for (int j = 0; j < count; ++j) {
+    js.job[j] = jobs[j];
+    const uint32_t t = (jobs[j].m + kScanTile - 1) / kScanTile;
+    one = one && t <= 1;
+    js.tile0[j + 1] = js.tile0[j] + (t ? t : 1);  // an empty job keeps one CTA (writes offsets[0])
+  }
+  for (int j = count + 1; j <= kMaxScanJobs; ++j) js.tile0[j] = js.tile0[count];
+  const uint32_t tiles = js.tile0[count];
+  if (one) {
+    k_scan_tiles_multi<true><<<tiles, kThreads, 0, s>>>(js);
+    note_launches(1);
+    return cudaGetLastError();
+  }
+  k_tile_sums_multi<<<tiles, kThreads, 0, s>>>(js);
+  k_scan_sums_multi<<<count, kThreads, 0, s>>>(js);
+  k_scan_tiles_multi<false><<<tiles, kThreads, 0, s>>>(js);
+  note_launches(3);
   return cudaGetLastError();
 }
 

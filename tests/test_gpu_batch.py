@@ -96,9 +96,18 @@ def test_batch_d2_matches_single_problem_calls(ctx):
         assert np.array_equal(np.sort(keys(got[:, 0], got[:, 1])), np.sort(keys(mine[:, 0], mine[:, 1])))
 
 
-def test_batch_async_in_cuda_graph(ctx):
+@pytest.mark.parametrize("small", [False, True])
+def test_batch_async_in_cuda_graph(ctx, small):
+    """Graph replay equals the plain call.  Under capture the sorts take
+    their recorded forms (one CTA for a small set, the multi-launch sort
+    otherwise) while the plain call uses the cooperative one: the pairs
+    must not differ."""
     import torch
-    inst = make_batch(2, 200, seed=5)
+    if small:   # every set below 8,192 extents
+        inst = [W.grid_random(int(n), int(m), 2, seed=40 + i, grid=6)
+                for i, (n, m) in enumerate(np.random.default_rng(3).integers(1, 150, size=(20, 2)))]
+    else:
+        inst = make_batch(2, 200, seed=5)
     K, p, po, (U, uo, so) = run_batch(ctx, inst)
     pairs = torch.zeros((K + 16, 2), dtype=torch.int32, device="cuda")
     pof = torch.zeros(len(inst) + 1, dtype=torch.int64, device="cuda")
