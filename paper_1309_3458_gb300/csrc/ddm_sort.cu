@@ -531,6 +531,209 @@ k_sort_grid(unsigned long long* __restrict__ keys0, uint32_t* __restrict__ vals0
   }
 }
 
+// Small sets (up to kClusterMax tiles of 512 * ITEMS keys): one thread-block
+// cluster holds the whole set in shared memory.  Each pass ranks a tile as
+// k_sort_grid does, writes its digit counts into every CTA's count table
+// (distributed shared memory), and after a cluster barrier scatters its
+// keys straight into the shared-memory tiles of their next owners; a second
+// cluster barrier ends the pass, and only the last pass writes to global
+// memory.  Both barriers are the hardware cluster barrier (no polling), and
+// no key goes through L2 between passes.
+constexpr uint32_t kClusterMax = 16;
+
+template <int ITEMS>
+struct ClusterSortSmem {
+  RankSmem r;
+  uint32_t gbase[kRadix];
+  uint32_t dtot[kRadix / 32];
+  uint32_t table[kClusterMax][kRadix];  // row j: CTA j's digit counts
+  unsigned long long tile_k[kSmallThreads * ITEMS];  // this CTA's keys of the next pass
+  uint32_t tile_v[kSmallThreads * ITEMS];
+  unsigned long long stage_k[kSmallThreads * ITEMS];  // this pass's keys in digit order
+  uint32_t stage_v[kSmallThreads * ITEMS];
+};
+
+__device__ __forceinline__ void cluster_sync_all() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;"
+               ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of `p` (this CTA's shared memory) in CTA `cta`'s shared memory.
+__device__ __forceinline__ uint32_t remote_smem(const void* p, uint32_t cta) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r) : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(cta));
+  return r;
+}
+__device__ __forceinline__ void st_remote(uint32_t a, uint32_t v) {
+  asm volatile("st.shared::cluster.u32 [%0], %1;" ::"r"(a), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_remote(uint32_t a, unsigned long long v) {
+  asm volatile("st.shared::cluster.u64 [%0], %1;" ::"r"(a), "l"(v) : "memory");
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kSmallThreads, 1)
+k_sort_cluster(const unsigned long long* __restrict__ in_k, const uint32_t* __restrict__ in_v,
+               unsigned long long* __restrict__ out_k, uint32_t* __restrict__ out_v, uint32_t n,
+               int passes) {
+  constexpr uint32_t kTile = kSmallThreads * ITEMS;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  ClusterSortSmem<ITEMS>& sm = *reinterpret_cast<ClusterSortSmem<ITEMS>*>(smem_raw);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t me = cluster_rank(), ctas = gridDim.x;  // the grid is one cluster
+  const uint32_t base = me * kTile;
+  const uint32_t valid = min(kTile, n - base);
+  unsigned long long key[ITEMS];
+  uint32_t val[ITEMS], dig[ITEMS], rank[ITEMS];
+#pragma unroll
+  for (int i = 0; i < ITEMS; ++i) {
+    const uint32_t local = warp * (ITEMS * 32) + i * 32 + lane;
+    key[i] = local < valid ? in_k[base + local] : 0ull;
+    val[i] = local < valid ? in_v[base + local] : 0u;
+  }
+  for (int p = 0; p < passes; ++p) {
+    const int shift = p * kRadixBits;
+    const uint32_t count = rank_tile<ITEMS>(sm.r, key, dig, rank, valid, shift);
+    if (tid < kRadix)
+      for (uint32_t j = 0; j < ctas; ++j) st_remote(remote_smem(&sm.table[me][tid], j), count);
+    cluster_sync_all();  // every table complete; every CTA holds its keys in registers
+    if (tid < kRadix) {  // the digit's first position, plus the CTAs before this one
+      uint32_t tot = 0, pre = 0;
+      for (uint32_t j = 0; j < ctas; ++j) {
+        const uint32_t c = sm.table[j][tid];
+        tot += c;
+        pre += j < me ? c : 0u;
+      }
+      uint32_t x = tot;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      if (lane == 31) sm.dtot[warp] = x;
+      sm.gbase[tid] = x - tot + pre - sm.r.lstart[tid];
+    }
+    __syncthreads();
+    if (tid < kRadix) {
+      uint32_t pre = 0;
+      for (int w = 0; w < warp; ++w) pre += sm.dtot[w];
+      sm.gbase[tid] += pre;
+    }
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      if (dig[i] < kRadix) {
+        const uint32_t slot = sm.r.lstart[dig[i]] + sm.r.whist[warp][dig[i]] + rank[i];
+        sm.stage_k[slot] = key[i];
+        sm.stage_v[slot] = val[i];
+      }
+    }
+    __syncthreads();
+    const bool last = p + 1 == passes;
+    // consecutive threads take consecutive slots: runs of one digit land in
+    // consecutive positions of one owner
+    for (uint32_t q = tid; q < valid; q += kSmallThreads) {
+      const unsigned long long k = sm.stage_k[q];
+      const uint32_t g = sm.gbase[(uint32_t)(k >> shift) & (kRadix - 1)] + q;
+      if (!DDM_IN_BOUNDS(g < n, nullptr)) continue;
+      if (last) {
+        out_k[g] = k;
+        out_v[g] = sm.stage_v[q];
+      } else {
+        const uint32_t owner = g / kTile, at = g % kTile;
+        st_remote(remote_smem(&sm.tile_k[at], owner), k);
+        st_remote(remote_smem(&sm.tile_v[at], owner), sm.stage_v[q]);
+      }
+    }
+    if (last) break;
+    cluster_sync_all();  // every key of the next pass is in its owner's tile
+#pragma unroll
+    for (int i = 0; i < ITEMS; ++i) {
+      const uint32_t local = warp * (ITEMS * 32) + i * 32 + lane;
+      key[i] = local < valid ? sm.tile_k[local] : 0ull;
+      val[i] = local < valid ? sm.tile_v[local] : 0u;
+    }
+  }
+}
+
+// Largest cluster (CTAs) k_sort_cluster<ITEMS> can run on the current
+// device: 16 (non-portable), else 8, else 0.
+template <int ITEMS>
+int cluster_sort_ctas() {
+  static std::atomic<int> best[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    cudaGetLastError();
+    return 0;
+  }
+  int b = best[dev].load(std::memory_order_relaxed);
+  if (b == 0) {
+    b = -1;
+    const size_t smem = sizeof(ClusterSortSmem<ITEMS>);
+    if (cudaFuncSetAttribute(k_sort_cluster<ITEMS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem) == cudaSuccess &&
+        cudaFuncSetAttribute(k_sort_cluster<ITEMS>,
+                             cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      for (int c : {16, 8}) {
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(c);
+        cfg.blockDim = dim3(kSmallThreads);
+        cfg.dynamicSmemBytes = smem;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = c;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int clusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&clusters, k_sort_cluster<ITEMS>, &cfg) == cudaSuccess &&
+            clusters > 0) {
+          b = c;
+          break;
+        }
+      }
+    }
+    cudaGetLastError();
+    best[dev].store(b, std::memory_order_relaxed);
+  }
+  return b < 0 ? 0 : b;
+}
+
+// One cluster launch of k_sort_cluster<ITEMS> if the set fits one cluster:
+// *done = true then (or an error), else nothing is enqueued.
+template <int ITEMS>
+cudaError_t try_sort_cluster(SortScratch sc, uint32_t n, int passes, cudaStream_t s, bool* done) {
+  *done = false;
+  constexpr uint32_t kTile = kSmallThreads * ITEMS;
+  const uint32_t ctas = (n + kTile - 1) / kTile;
+  if (ctas > (uint32_t)cluster_sort_ctas<ITEMS>()) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(ctas);
+  cfg.blockDim = dim3(kSmallThreads);
+  cfg.dynamicSmemBytes = sizeof(ClusterSortSmem<ITEMS>);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = ctas;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  const int out = passes & 1;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, k_sort_cluster<ITEMS>, sc.keys[0], sc.vals[0],
+                                     sc.keys[out], sc.vals[out], n, passes);
+  if (e == cudaSuccess) {
+    note_launches(1);
+    *done = true;
+  }
+  return e;
+}
+
 // Co-resident CTAs of k_sort_grid<ITEMS> on the current device, capped at
 // kGridMaxTiles (0: not usable).
 template <int ITEMS>
@@ -611,14 +814,19 @@ cudaError_t launch_sort64(SortScratch sc, uint32_t n, int passes, int* out_buf, 
   cudaError_t e;
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if ((e = cudaStreamIsCapturing(s, &cap))) return e;
-  // One cooperative launch when every tile can be resident at once, with
-  // the smallest tile that allows it.  Measured (8 passes, one GB300):
-  // 8,192 keys 49 us against 55 in one CTA; 25,000 keys 57 us (2,048-key
-  // tiles) against 94 (8,192-key tiles); 250,000 keys 76 against 105.
-  // Not under stream capture: the single-CTA or multi-launch form is
-  // recorded instead.
+  // Up to 16 tiles of 2,048 keys: one cluster, keys kept on chip; else one
+  // cooperative launch when every tile can be resident at once, with the
+  // smallest tile that allows it.  Measured (8 passes, one GB300): 5,000
+  // keys 33 us in a cluster, 53 cooperative, 51 in one CTA; 25,000 keys 41,
+  // 57 (2,048-key tiles) and 100 (8,192-key tiles); 250,000 keys 76
+  // cooperative.  Not under stream capture: the single-CTA or multi-launch
+  // form is recorded instead.
   if (cap == cudaStreamCaptureStatusNone) {
     bool done = false;
+    if ((e = try_sort_cluster<4>(sc, n, passes, s, &done)) || done) {
+      *out_buf = passes & 1;
+      return e;
+    }
     if ((e = try_sort_grid<4>(sc, n, passes, st, sms, s, &done)) || done) {
       *out_buf = passes & 1;
       return e;

@@ -1,9 +1,10 @@
 """Sort sizes around the kernels' thresholds (GPU).
 
-The radix sort takes one of several forms by size: one cooperative launch
-with tiles of 2,048, 4,096 or 8,192 keys while every tile can be resident
-(up to 1,245,184 keys on a 152-SM GB300), the multi-launch onesweep beyond
-(and one CTA for up to 8,192 keys under stream capture).  For d = 1
+The radix sort takes one of several forms by size: one thread-block
+cluster for up to 16 x 2,048 keys, one cooperative launch with tiles of
+2,048, 4,096 or 8,192 keys while every tile can be resident (up to
+1,245,184 keys on a 152-SM GB300), the multi-launch onesweep beyond (and one
+CTA for up to 8,192 keys under stream capture).  For d = 1
 both orders are fixed exactly: the tree order is the lexicographic order of
 (lower bound, upper bound, id) under the IEEE total order with -0 = +0
 (Section IV's sort by lower bound, ties as the stable passes leave them),
@@ -21,7 +22,7 @@ from tests.test_gpu_parity import order_key
 
 pytestmark = pytest.mark.gpu
 
-SIZES = [2, 33, 2048, 2049, 4097, 8192, 8193, 16384, 16385, 100_003, 311_296, 311_297,
+SIZES = [2, 33, 2048, 2049, 4097, 8192, 8193, 16385, 32768, 32769, 100_003, 311_296, 311_297,
          1_245_184, 1_245_185, 1_500_000]
 
 
