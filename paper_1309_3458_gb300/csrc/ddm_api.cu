@@ -467,10 +467,10 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
   c->arena = RecordArena{};
   if (record && c->replay_on && m > 0 && c->tree.n > 0 && c->replay_budget > 0) {
     const uint32_t packets = packets_of(c, m);
-    // bytes per block: records (three words each), next/count/packet/list entries
-    const uint64_t per_block = (uint64_t)kRecBlock * 3 * sizeof(uint32_t) + 4 * sizeof(uint32_t);
+    // bytes per block: records (ten bytes each) and header, next/count/packet/list entries
+    const uint64_t per_block = (uint64_t)kRecWords * sizeof(uint32_t) + 4 * sizeof(uint32_t);
     // Blocks the arena holds now, and what the latest recorded pass needed.
-    uint64_t have = c->rec.cap / ((size_t)kRecBlock * 3 * sizeof(uint32_t));
+    uint64_t have = c->rec.cap / ((size_t)kRecWords * sizeof(uint32_t));
     for (const DevBuf* b : {&c->blk_next, &c->blk_count, &c->blk_pkt, &c->blk_list})
       have = std::min<uint64_t>(have, b->cap / sizeof(uint32_t));
     const uint32_t hint_blocks = c->rec_hint[0], hint_packets = c->rec_hint[1],
@@ -491,7 +491,7 @@ int plan_async(ddm_ctx* c, const float* ulo, const float* uhi, uint32_t m, uint3
     const uint64_t cap_blocks = c->replay_budget / per_block;
     if (want > cap_blocks) want = cap_blocks;
     if (want > 0xfffffff0ull) want = 0xfffffff0ull;
-    if (want > 0 && ensure(c, c->rec, (size_t)want * kRecBlock * 3 * sizeof(uint32_t)) == DDM_OK &&
+    if (want > 0 && ensure(c, c->rec, (size_t)want * kRecWords * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_next, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_count, (size_t)want * sizeof(uint32_t)) == DDM_OK &&
         ensure(c, c->blk_pkt, (size_t)want * sizeof(uint32_t)) == DDM_OK &&

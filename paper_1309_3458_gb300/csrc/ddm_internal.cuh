@@ -215,16 +215,22 @@ cudaError_t launch_export_nodes(const TreeView& t, float* node_lo, float* node_h
 
 // ---- ddm_query.cu ---------------------------------------------------------
 // Replay records.  While counting, every (query, leaf) test of a packet
-// that has hits is stored as one record of three words: x = leaf << 5 |
-// query lane, hit mask over the leaf's 32 subscriptions, and the query's
-// matches before this leaf (so the record knows where its pairs go in the
-// query's output).  Records of a packet are kept in walk order (leaf by
-// leaf, query lanes ascending within a leaf), in chains of fixed-size
-// blocks taken from a shared arena; a block stores its packet.  After
-// counting, the blocks are listed in plan order and the write pass expands
-// any range of them, every record independently, instead of walking the
-// tree again.
-constexpr uint32_t kRecBlock = 512;       // records per block (3 x 2 KiB, one array per word)
+// that has hits is stored as one record of ten bytes: x = leaf << 5 | query
+// lane, the hit mask over the leaf's 32 subscriptions, and (16 bits) the
+// query's matches before this leaf counted from the start of the record's
+// block.  Records of a packet are kept in walk order (leaf by leaf, query
+// lanes ascending within a leaf), in chains of fixed-size blocks taken from a
+// shared arena; a block stores its packet, and a header with the matches each
+// query of its chain had before the block's first record, so that a record's
+// place in its query's output is the header entry plus its 16-bit count (a
+// block holds at most 512 records of at most 32 hits: the count stays below
+// 2^14).  After counting, the blocks are listed in plan order and the write
+// pass expands any range of them, every record independently, instead of
+// walking the tree again.
+constexpr uint32_t kRecBlock = 512;  // records per block: x and hit mask 2 KiB each, counts 1 KiB
+constexpr uint32_t kRecHdr = 16;     // header: one running count per query of the chain
+// words per block: x[kRecBlock], hit mask[kRecBlock], 16-bit counts, header
+constexpr uint32_t kRecWords = 2 * kRecBlock + kRecBlock / 2 + kRecHdr;
 // A packet's records go to two chains of blocks, one per half of its query
 // lanes, so that a block holds the records of at most 16 queries (its pairs
 // land in fewer output runs): the write pass took 127 instead of 134 ms on
@@ -233,7 +239,7 @@ constexpr uint32_t kRecBlock = 512;       // records per block (3 x 2 KiB, one a
 constexpr uint32_t kRecChains = 2;
 constexpr uint32_t kNoBlock = 0xffffffffu;
 struct RecordArena {
-  uint32_t* rec;           // [max_blocks][3][kRecBlock]: x, hit mask, matches before
+  uint32_t* rec;           // [max_blocks][kRecWords]: x, hit mask, 16-bit counts, header
   uint32_t* blk_next;      // [max_blocks] next block of the chain, or kNoBlock
   uint32_t* blk_count;     // [max_blocks] records in the block
   uint32_t* blk_pkt;       // [max_blocks] packet of the block

@@ -266,6 +266,7 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
     bool rec_write = recording;
     uint32_t cur0 = kNoBlock, cur1 = kNoBlock, fill0 = kRecBlock, fill1 = kRecBlock;
     uint32_t nblk0 = 0, nblk1 = 0;
+    uint32_t blk_cnt = 0;  // this query's matches before its chain's current block
     // Test the 32 level-1 nodes (leaves) from g1 on against the packet box,
     // then run the packet's queries over each surviving leaf.
     auto leaves = [&](uint32_t g1) {
@@ -523,6 +524,11 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
                     }
                     ra.blk_pkt[b] = p;
                   }
+                  // header: the chain's queries' matches before this leaf
+                  if ((uint32_t)(lane >> 4) == (uint32_t)ch) {
+                    ra.rec[(size_t)b * kRecWords + 2u * kRecBlock + kRecBlock / 2u + (lane & 15)] = cnt;
+                    blk_cnt = cnt;
+                  }
                   cb = b;
                 }
               }
@@ -533,10 +539,11 @@ k_packets(TreeView t, QueryView q, BatchView bv, uint32_t* __restrict__ counts,
             const bool hi = lane >= 16;
             const uint32_t at = (hi ? fill1 + __popc(rm & lt & 0xffff0000u) : fill0 + __popc(rm & lt));
             if (DDM_IN_BOUNDS(at < kRecBlock && (hi ? cur1 : cur0) < ra.max_blocks, st)) {
-              uint32_t* r = ra.rec + (size_t)(hi ? cur1 : cur0) * (3u * kRecBlock) + at;
-              r[0] = ((g1 + cl) << 5) | (uint32_t)lane;
-              r[kRecBlock] = my_hb;
-              r[2u * kRecBlock] = cnt;  // this query's matches before the leaf
+              uint32_t* r = ra.rec + (size_t)(hi ? cur1 : cur0) * kRecWords;
+              r[at] = ((g1 + cl) << 5) | (uint32_t)lane;
+              r[kRecBlock + at] = my_hb;
+              // this query's matches before the leaf, from the block's start
+              reinterpret_cast<uint16_t*>(r + 2u * kRecBlock)[at] = (uint16_t)(cnt - blk_cnt);
             }
           }
           fill0 += k0;
@@ -668,6 +675,11 @@ __device__ __forceinline__ uint32_t ld_hinted(const uint32_t* a, unsigned long l
   asm("ld.global.nc.L2::cache_hint.u32 %0, [%1], %2;" : "=r"(v) : "l"(a), "l"(policy));
   return v;
 }
+__device__ __forceinline__ uint32_t ld_hinted(const uint16_t* a, unsigned long long policy) {
+  unsigned short v;
+  asm("ld.global.nc.L2::cache_hint.u16 %0, [%1], %2;" : "=h"(v) : "l"(a), "l"(policy));
+  return v;
+}
 __device__ __forceinline__ void st_hinted(ddm_pair* a, ddm_pair v, unsigned long long policy) {
   asm volatile("st.global.L2::cache_hint.v2.u32 [%0], {%1, %2}, %3;" ::"l"(a), "r"(v.upd),
                "r"(v.sub), "l"(policy)
@@ -683,9 +695,10 @@ __device__ __forceinline__ void st_hinted(uint32_t* a, uint32_t v, unsigned long
 // list, so uneven packets spread over the whole GPU.  A warp loads the
 // block's packet queries (their output offsets) and takes the records 32 at
 // a time (the next 32 are loaded while these expand), one per lane: each lane
-// works out where its record's pairs go (its query's offset plus the matches
-// the count pass had found before the record) and leaves (leaf, hit mask,
-// update id, position) in shared memory.  The warp then expands the 32
+// works out where its record's pairs go (its query's offset, plus the block
+// header's count of the query's matches before the block, plus the record's
+// own count of them since) and leaves (leaf, hit mask, update id, position)
+// in shared memory.  The warp then expands the 32
 // records one after another with lane = leaf slot, each record's fields read
 // by one broadcast from shared memory: the lanes whose bit is set in the hit
 // mask load their subscription ids (one 128-byte load for the whole leaf) and
@@ -781,22 +794,30 @@ k_replay(TreeView t, QueryView q, BatchView bv, RecordArena ra, WriteView w, uin
     const uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     if (vmask == 0u) continue;
     const uint32_t nrec = ra.blk_count[blk];
-    const uint32_t* rec = ra.rec + (size_t)blk * (3u * kRecBlock);
-    uint32_t nx = 0u, nhb = 0u, nbef = 0u;
+    const uint32_t* rec = ra.rec + (size_t)blk * kRecWords;
+    const uint16_t* rel = reinterpret_cast<const uint16_t*>(rec + 2u * kRecBlock);
+    uint32_t nx = 0u, nhb = 0u, nrel = 0u;
     if (lane < nrec) {
       nx = ld_hinted(&rec[lane], stream);
       nhb = ld_hinted(&rec[kRecBlock + lane], stream);
-      nbef = ld_hinted(&rec[2u * kRecBlock + lane], stream);
+      nrel = ld_hinted(&rel[lane], stream);
     }
+    // the block header: lane j holds the matches query j of the chain had
+    // before the block
+    const uint32_t hdr =
+        lane < (int)kRecHdr ? ld_hinted(&rec[2u * kRecBlock + kRecBlock / 2u + lane], stream) : 0u;
     for (uint32_t r0 = 0; r0 < nrec; r0 += 32u) {
-      const uint32_t x = nx, bef = nbef;
+      const uint32_t x = nx, xrel = nrel;
       uint32_t hb = nhb;
+      nx = nhb = nrel = 0u;  // lanes past the block's last record hold x = hb = 0
       if (r0 + 32u + lane < nrec) {
         nx = ld_hinted(&rec[r0 + 32u + lane], stream);
         nhb = ld_hinted(&rec[kRecBlock + r0 + 32u + lane], stream);
-        nbef = ld_hinted(&rec[2u * kRecBlock + r0 + 32u + lane], stream);
+        nrel = ld_hinted(&rel[r0 + 32u + lane], stream);
       }
       const int qq = (int)(x & 31u);
+      // the query's matches before this record: header + the record's count
+      const uint32_t bef = __shfl_sync(0xffffffffu, hdr, qq & (int)(kRecHdr - 1)) + xrel;
       if (!((vmask >> qq) & 1u)) hb = 0u;  // also clears lanes past nrec (x = hb = 0)
       const Cursor o = __shfl_sync(0xffffffffu, out, qq) + (Cursor)bef;
       const uint32_t Qq = __shfl_sync(0xffffffffu, Qout, qq);
