@@ -45,8 +45,8 @@ DEFAULT_CONFIG = "clustered_d3_N1e7_a100"
 # (a smaller case of the same workload; traffic scales with pairs written),
 # and per id of the compressed output's kernel
 # (profiles/k_replay_ids_clustered_d3_scale0.15.md).
-TRAFFIC_PER_PAIR = 8.86
-TRAFFIC_PER_ID = 5.49
+TRAFFIC_PER_PAIR = 8.76
+TRAFFIC_PER_ID = 5.37
 METRIC = "matched pairs/s (N=1e7, alpha=100, d=3)"
 PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
 
