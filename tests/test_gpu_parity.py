@@ -368,6 +368,43 @@ def test_replay_and_walking_write_agree(ctx):
     assert np.array_equal(np.sort(keys(full[:, 0], full[:, 1])), np.sort(keys(ou, os_)))
 
 
+@pytest.mark.parametrize("wide", [1, 16])
+def test_replay_record_counts_at_block_limits(ctx, wide):
+    """Records carry their query's matches since the start of their block in
+    16 bits, above a per-block header.  One query (wide = 1) meeting all of
+    40,000 points fills whole 512-record blocks of 32-hit records alone, so
+    the count reaches 511 x 32 in each block; sixteen such queries (wide =
+    16) share every block.  Pairs and compressed ids against the oracle."""
+    import torch
+    n = 40000
+    slo = np.arange(n, dtype=np.float32)[None, :].copy()
+    shi = slo.copy()
+    m = 40
+    ulo = np.full((1, m), 2e6, np.float32)     # lanes past `wide` meet nothing
+    uhi = np.full((1, m), 2e6, np.float32)
+    ulo[0, :wide] = -1.0 - np.arange(wide, dtype=np.float32)
+    uhi[0, :wide] = 1e6
+    arrays = (ulo, uhi, slo, shi)
+    K, pu, ps = gpu_match(ctx, arrays)
+    Ko, ou, os_ = oracle.itm_pairs(*arrays)
+    assert K == Ko == wide * n
+    assert np.array_equal(pu, ou) and np.array_equal(ps, os_)
+    U = to_dev(arrays)
+    ddm.ddm_build(ctx, U[2], U[3])
+    assert ddm.ddm_plan(ctx, U[0], U[1]) == K
+    order = torch.empty(m, dtype=torch.int32, device="cuda")
+    ooff = torch.empty(m + 1, dtype=torch.int64, device="cuda")
+    ddm.ddm_plan_order(ctx, order, ooff)
+    ids = torch.empty(K, dtype=torch.int32, device="cuda")
+    assert ddm.ddm_write_ordered_ids(ctx, 0, m, ids) == K
+    order = order.cpu().numpy()
+    ooff = ooff.cpu().numpy()
+    ids = ids.cpu().numpy().view(np.uint32)
+    for p in range(m):
+        u = order[p]
+        assert np.array_equal(ids[ooff[p]:ooff[p + 1]], os_[ou == u])
+
+
 # --- error paths -------------------------------------------------------------
 
 def test_invalid_extents(ctx):
