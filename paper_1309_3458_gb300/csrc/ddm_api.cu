@@ -304,7 +304,8 @@ int order_set_batch(ddm_ctx* c, int d, const float* lo, const float* hi, uint32_
     DDM_CUDA(launch_rekey_batch(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt,
                                 cnt, bs.inst, bs.off, gl, gb,
                                 static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
-    DDM_TRY(sort_pass(c, cnt, 3 + key_bytes(cnt), cur, s));  // at most cnt groups
+    // groups: at most one per instance without re-sort plus cnt / 64
+    DDM_TRY(sort_pass(c, cnt, 3 + key_bytes((uint64_t)bs.count + cnt / 64), cur, s));
   }
   return DDM_OK;
 }
@@ -344,7 +345,8 @@ int order_set_classes(ddm_ctx* c, int d, const float* lo, const float* hi, uint3
     DDM_CUDA(launch_rekey_batch(static_cast<const uint32_t*>(c->vals[*cur].p), lo + (size_t)k * cnt,
                                 cnt, inst, off, gl, gb,
                                 static_cast<unsigned long long*>(c->keys[*cur].p), c->sms, s));
-    DDM_TRY(sort_pass(c, cnt, 3 + key_bytes(cnt), cur, s));  // at most cnt groups
+    // groups: at most one per class without re-sort plus cnt / 64
+    DDM_TRY(sort_pass(c, cnt, 3 + key_bytes((uint64_t)kClasses + cnt / 64), cur, s));
   }
   return DDM_OK;
 }

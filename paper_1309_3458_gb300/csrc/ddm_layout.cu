@@ -167,7 +167,10 @@ __global__ void k_batch_groups(const unsigned long long* __restrict__ off, uint3
       if (gp > 0 && g >= gp) g = 0;
     }
     glog2[i] = g;
-    ngroups[i] = g > 0 ? ((n + (1u << g) - 1) >> g) : n;  // g == 0: groups of one
+    // g == 0 (no re-sort): the whole instance is one group whose keys are
+    // all equal, so the stable sort keeps it in place.  With g >= 6 every
+    // instance has at most n / 64 + 1 groups.
+    ngroups[i] = g > 0 ? ((n + (1u << g) - 1) >> g) : (n > 0 ? 1u : 0u);
   }
 }
 
@@ -179,8 +182,13 @@ k_rekey_batch(const uint32_t* __restrict__ vals, const float* __restrict__ lo_k,
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += stride) {
     const uint32_t b = inst[i];
+    const int g = glog2[b];
+    if (g == 0) {  // one group, equal keys: the instance keeps its order
+      keys[i] = gbase[b] << kLocalityBits;
+      continue;
+    }
     const unsigned long long local = i - off[b];
-    const unsigned long long group = gbase[b] + (local >> glog2[b]);
+    const unsigned long long group = gbase[b] + (local >> g);
     keys[i] = (group << kLocalityBits) | (float_key(__ldg(lo_k + vals[i])) >> kLocalityDrop);
   }
 }
