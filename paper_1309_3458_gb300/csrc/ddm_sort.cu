@@ -379,30 +379,34 @@ k_sort_small(const unsigned long long* __restrict__ in_keys, const uint32_t* __r
 // resident): one cooperative launch runs every pass.  CTA g holds tile g in
 // registers and ranks it as k_sort_small does; the tiles then exchange their
 // digit counts through global memory across a grid barrier, each CTA takes
-// its digit offsets from all earlier tiles' counts (no look-back chain),
-// scatters, and a second barrier ends the pass.  Per-tile counts are < 2^16
-// and travel packed two to a word; the whole table (tiles x 512 bytes) is
-// read into shared memory.  Smaller tiles (fewer items per thread) spread a
-// set over more SMs: each pass's ranking and scatter shrink with the tile,
-// the two barriers do not.
-constexpr uint32_t kGridMaxTiles = 192;  // table: 192 x 512 B = 96 KiB
+// its digit offsets from the counts (no look-back chain), scatters, and a
+// second barrier ends the pass.  Tiles come in groups of kGridGroup: a tile
+// adds its counts into its group's sums (global atomics) and stores them,
+// 16-bit and packed two to a word, in its own row; a digit's total is the
+// sum of the group sums and the part before tile g the sums of the groups
+// before g's plus the rows of g's group before it -- at most 12 + 15 reads
+// per digit instead of one per tile.  The group sums are double-buffered by
+// pass parity, and each pass clears the buffer of the next.  Smaller tiles
+// (fewer items per thread) spread a set over more SMs: each pass's ranking
+// and scatter shrink with the tile, the two barriers do not.
+constexpr uint32_t kGridMaxTiles = 192;
+constexpr uint32_t kGridGroup = 16;
+constexpr uint32_t kGridGroups = kGridMaxTiles / kGridGroup;  // 12
+// Scratch words of a cooperative sort after the per-tile rows: group sums
+// of both parities, then the barrier counter (zeroed before each launch).
+constexpr size_t kGridRowWords = (size_t)kGridMaxTiles * (kRadix / 2);
+constexpr size_t kGridSumWords = 2 * (size_t)kGridGroups * kRadix;
+constexpr size_t kGridScratchWords = kGridRowWords + kGridSumWords + 32;
 
 template <int ITEMS>
 struct GridSortSmem {
   RankSmem r;
   uint32_t gbase[kRadix];
-  uint32_t part_tot[2][kRadix];
-  uint32_t part_pre[2][kRadix];
   uint32_t dtot[kRadix / 32];
   int abort;
   int pad[3];
-  union {
-    struct {
-      unsigned long long keys[kSmallThreads * ITEMS];
-      uint32_t vals[kSmallThreads * ITEMS];
-    } stage;
-    uint4 table[kGridMaxTiles * kRadix / 8];  // per tile: 256 16-bit counts
-  } u;
+  unsigned long long keys[kSmallThreads * ITEMS];
+  uint32_t vals[kSmallThreads * ITEMS];
 };
 
 // Grid-wide barrier for a cooperative launch (all CTAs resident).  `bar` is
@@ -468,31 +472,29 @@ k_sort_grid(unsigned long long* __restrict__ keys0, uint32_t* __restrict__ vals0
     }
     const int shift = p * kRadixBits;
     const uint32_t count = rank_tile<ITEMS>(sm.r, key, dig, rank, valid, shift);
-    if (tid < kRadix) {  // this tile's counts, two 16-bit digits per word
+    uint32_t* gsum = table + kGridRowWords + (size_t)(p & 1) * kGridGroups * kRadix;
+    if (tid < kRadix) {  // this tile's counts: its row (two 16-bit digits per word), its group's sums
       const uint32_t next = __shfl_down_sync(0xffffffffu, count, 1);
       if ((tid & 1) == 0) __stcg(table + (size_t)tile * (kRadix / 2) + tid / 2, count | (next << 16));
+      if (count) atomicAdd(&gsum[(tile / kGridGroup) * kRadix + tid], count);
     }
     if (!grid_barrier(bar, tiles * ++barriers, st, &sm.abort)) return;
-    // every tile's counts into shared memory (coalesced 16-byte loads)
-    const uint4* t4 = reinterpret_cast<const uint4*>(table);
-    for (uint32_t q = tid; q < tiles * (kRadix / 8); q += kSmallThreads) sm.u.table[q] = __ldcg(t4 + q);
-    __syncthreads();
-    {  // digit tid & 255 over half of the tiles: total, and the part before this tile
-      const int dg = tid & (kRadix - 1), h = tid >> 8;
-      const uint32_t half = (tiles + 1) / 2, g0 = h * half, g1 = min(tiles, g0 + half);
-      const uint32_t* tw = reinterpret_cast<const uint32_t*>(sm.u.table);
-      uint32_t tot = 0, pre = 0;
-      for (uint32_t g = g0; g < g1; ++g) {
-        const uint32_t c = (tw[g * (kRadix / 2) + dg / 2] >> ((dg & 1) * 16)) & 0xffffu;
-        tot += c;
-        pre += g < tile ? c : 0u;
-      }
-      sm.part_tot[h][dg] = tot;
-      sm.part_pre[h][dg] = pre;
+    {  // clear the next pass's group sums (last read in the previous pass)
+      uint32_t* other = table + kGridRowWords + (size_t)((p + 1) & 1) * kGridGroups * kRadix;
+      for (uint32_t q = tile * kSmallThreads + tid; q < kGridGroups * kRadix; q += tiles * kSmallThreads)
+        other[q] = 0u;
     }
-    __syncthreads();
-    if (tid < kRadix) {  // exclusive scan of the digit totals: the digit's first position
-      const uint32_t tot = sm.part_tot[0][tid] + sm.part_tot[1][tid];
+    if (tid < kRadix) {  // digit tid: its total, and the part before this tile
+      const uint32_t groups = (tiles + kGridGroup - 1) / kGridGroup, mine = tile / kGridGroup;
+      uint32_t tot = 0, pre = 0;
+      for (uint32_t g = 0; g < groups; ++g) {
+        const uint32_t c = __ldcg(gsum + g * kRadix + tid);
+        tot += c;
+        pre += g < mine ? c : 0u;
+      }
+      for (uint32_t t = mine * kGridGroup; t < tile; ++t)
+        pre += (__ldcg(table + (size_t)t * (kRadix / 2) + tid / 2) >> ((tid & 1) * 16)) & 0xffffu;
+      // exclusive scan of the digit totals: the digit's first position
       uint32_t x = tot;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -500,7 +502,7 @@ k_sort_grid(unsigned long long* __restrict__ keys0, uint32_t* __restrict__ vals0
         if (lane >= o) x += y;
       }
       if (lane == 31) sm.dtot[warp] = x;
-      sm.gbase[tid] = x - tot + sm.part_pre[0][tid] + sm.part_pre[1][tid] - sm.r.lstart[tid];
+      sm.gbase[tid] = x - tot + pre - sm.r.lstart[tid];
     }
     __syncthreads();
     if (tid < kRadix) {
@@ -513,18 +515,18 @@ k_sort_grid(unsigned long long* __restrict__ keys0, uint32_t* __restrict__ vals0
     for (int i = 0; i < ITEMS; ++i) {
       if (dig[i] < kRadix) {
         const uint32_t slot = sm.r.lstart[dig[i]] + sm.r.whist[warp][dig[i]] + rank[i];
-        sm.u.stage.keys[slot] = key[i];
-        sm.u.stage.vals[slot] = val[i];
+        sm.keys[slot] = key[i];
+        sm.vals[slot] = val[i];
       }
     }
     __syncthreads();
     // ... and out, consecutive threads taking consecutive slots
     for (uint32_t q = tid; q < valid; q += kSmallThreads) {
-      const unsigned long long k = sm.u.stage.keys[q];
+      const unsigned long long k = sm.keys[q];
       const uint32_t g = sm.gbase[(uint32_t)(k >> shift) & (kRadix - 1)] + q;
       if (DDM_IN_BOUNDS(g < n, st)) {
         ok[g] = k;
-        ov[g] = sm.u.stage.vals[q];
+        ov[g] = sm.vals[q];
       }
     }
     if (p + 1 < passes && !grid_barrier(bar, tiles * ++barriers, st, &sm.abort)) return;
@@ -769,7 +771,9 @@ cudaError_t try_sort_grid(SortScratch sc, uint32_t n, int passes, Status* st, in
   const uint32_t tiles = (n + kTile - 1) / kTile;
   if (tiles > (uint32_t)grid_sort_tiles<ITEMS>(sms)) return cudaSuccess;
   cudaError_t e;
-  if ((e = cudaMemsetAsync(sc.counters, 0, sizeof(uint32_t), s))) return e;
+  // both parities' group sums and the barrier counter start at zero
+  uint32_t* sums = sc.lookback + kGridRowWords;
+  if ((e = cudaMemsetAsync(sums, 0, sizeof(uint32_t) * (kGridSumWords + 1), s))) return e;
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(tiles);
   cfg.blockDim = dim3(kSmallThreads);
@@ -781,7 +785,7 @@ cudaError_t try_sort_grid(SortScratch sc, uint32_t n, int passes, Status* st, in
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   e = cudaLaunchKernelEx(&cfg, k_sort_grid<ITEMS>, sc.keys[0], sc.vals[0], sc.keys[1], sc.vals[1],
-                         n, passes, sc.lookback, sc.counters, st);
+                         n, passes, sc.lookback, sums + kGridSumWords, st);
   if (e == cudaErrorCooperativeLaunchTooLarge) {  // fewer SMs available than counted
     cudaGetLastError();
     return cudaSuccess;
@@ -803,7 +807,8 @@ cudaError_t launch_debug_wait(const uint32_t* word, uint32_t limit, Status* st, 
 
 size_t sort_lookback_words(uint32_t n) {
   const size_t tiles = ((size_t)n + kSortTile - 1) / kSortTile;
-  return (size_t)kPasses * tiles * kRadix;
+  // the onesweep look-back words, or the cooperative sort's rows, group sums and counter
+  return std::max((size_t)kPasses * tiles * kRadix, kGridScratchWords);
 }
 
 cudaError_t launch_sort64(SortScratch sc, uint32_t n, int passes, int* out_buf, Status* st,
