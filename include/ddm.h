@@ -378,7 +378,8 @@ int ddm_tree_export(ddm_ctx *ctx, uint32_t *order, float *node_lo, float *node_h
 
 /* Record budget of the write pass.  While counting, ddm_plan (and the
  * one-shot calls) can keep a compact record of every (update, leaf) test
- * that found pairs -- 8 bytes per record, about one record per 6-8 pairs --
+ * that found pairs -- 10 bytes per record plus 64 bytes per block of 512
+ * records, about one record per 12 pairs on clustered d = 3 extents --
  * so that the write pass expands the records instead of walking the tree a
  * second time.  The records live in a context arena of at most `bytes`
  * (default: a quarter of the device's memory); the arena is sized from what
