@@ -188,14 +188,15 @@ struct SortScratch {
   unsigned long long* keys[2];
   uint32_t* vals[2];
   uint32_t* hist;       // [8][256]
-  uint32_t* lookback;   // [8][tiles][256]
+  uint32_t* lookback;   // [8][tiles][256], or the cooperative sort's scratch
   uint32_t* counters;   // [8]
 };
 constexpr int kSortTile = 4096;
 size_t sort_lookback_words(uint32_t n);
-// Stable LSD onesweep radix sort on the low 8*passes bits of 64-bit keys,
-// with a uint32 payload.  Input in keys[0]/vals[0]; *out_buf receives the
-// index (0 or 1) of the buffers holding the result.
+// Stable LSD radix sort on the low 8*passes bits of 64-bit keys, with a
+// uint32 payload (one cluster, one cooperative launch or onesweep, by size).
+// Input in keys[0]/vals[0]; *out_buf receives the index (0 or 1) of the
+// buffers holding the result.
 // Test hook: one warp polls `word` (which nothing sets) with the sort's
 // bounded wait, at most `limit` polls, and records kErrTimeout.
 cudaError_t launch_debug_wait(const uint32_t* word, uint32_t limit, Status* st, cudaStream_t s);

@@ -1,19 +1,28 @@
-// Onesweep LSD radix sort of 64-bit keys with a 32-bit payload.
+// LSD radix sort of 64-bit keys with a 32-bit payload.
 //
 // Sorts the subscriptions into the interval tree order of Section IV (lower
 // bound, then upper bound; the stable passes keep remaining ties in id
-// order).  Design (after Adinets & Merrill, "Onesweep", 2022):
-//   1. one histogram pass over the keys computes all eight 8-bit digit
-//      histograms at once; a tiny kernel scans them into digit bases;
-//   2. each digit pass is ONE kernel: a CTA takes the next tile (ticket from
-//      an atomic counter, so every earlier tile is already resident), ranks
-//      its keys per digit with a warp match (one ballot per digit bit) and
-//      per-warp counters, publishes its
-//      per-digit counts, resolves its global per-digit offsets by decoupled
-//      look-back over earlier tiles, and scatters through shared memory so
-//      that global stores come out as runs of equal digits.
-// Look-back waits are bounded: after kSpinLimit polls a CTA records
-// kErrTimeout and carries on, so the kernel always terminates.
+// order), and the updates and the re-sorts into locality orders.  Three
+// forms by size, each a stable sort over 8-bit digits:
+//   * up to 16 tiles of 2,048 keys: one thread-block cluster keeps the keys
+//     in distributed shared memory for every pass (k_sort_cluster);
+//   * up to one resident tile per SM: one cooperative launch runs every pass,
+//     the tiles exchanging digit counts across bounded grid barriers
+//     (k_sort_grid);
+//   * beyond (and under stream capture): onesweep, after Adinets & Merrill
+//     ("Onesweep", 2022): one histogram pass over the keys computes all eight
+//     8-bit digit histograms at once, a tiny kernel scans them into digit
+//     bases, and each digit pass is ONE kernel: a CTA takes the next tile
+//     (ticket from an atomic counter, so every earlier tile is already
+//     resident), ranks its keys per digit with a warp match (one ballot per
+//     digit bit) and per-warp counters, publishes its per-digit counts,
+//     resolves its global per-digit offsets by decoupled look-back over
+//     earlier tiles, and scatters through shared memory so that global
+//     stores come out as runs of equal digits.  Under stream capture, sets of
+//     up to 8,192 keys take one CTA instead (k_sort_small).
+// Every wait is bounded: after kSpinLimit polls a CTA records kErrTimeout and
+// carries on (look-back) or returns (grid barrier), so the kernels always
+// terminate.
 #include <algorithm>
 #include <atomic>
 
