@@ -401,8 +401,9 @@ k_sort_small(const unsigned long long* __restrict__ in_keys, const uint32_t* __r
 constexpr uint32_t kGridMaxTiles = 192;
 constexpr uint32_t kGridGroup = 16;
 constexpr uint32_t kGridGroups = kGridMaxTiles / kGridGroup;  // 12
-// Scratch words of a cooperative sort after the per-tile rows: group sums
-// of both parities, then the barrier counter (zeroed before each launch).
+// Scratch words of a cooperative sort: the per-tile rows, the group sums of
+// both parities and the barrier counter (the last two zeroed before each
+// launch).
 constexpr size_t kGridRowWords = (size_t)kGridMaxTiles * (kRadix / 2);
 constexpr size_t kGridSumWords = 2 * (size_t)kGridGroups * kRadix;
 constexpr size_t kGridScratchWords = kGridRowWords + kGridSumWords + 32;
