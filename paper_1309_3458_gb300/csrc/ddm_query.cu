@@ -732,6 +732,8 @@ struct ReplayShape {
   static constexpr int ctas = OUT == 2 ? 4 : 2;
   static constexpr int group = OUT == 2 ? 8 : 16;
   static constexpr bool dense = OUT == 2;
+  // a round of 32 records is expanded in whole groups
+  static_assert(32 % group == 0, "records in flight must divide a round of 32");
 };
 template <bool FILTER_ID, bool WIDE, bool BATCH, int OUT>
 __global__ void __launch_bounds__(kThreads, ReplayShape<OUT>::ctas)
