@@ -66,3 +66,20 @@ def test_reference_arm_prints_the_contract_line():
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1
     assert d["e2e"] == {"value": d["value"], "unit": "pairs/s", "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
+
+
+def test_cpu_baseline_small_and_config2_legs():
+    """The oracle legs the bench adds to `cpu_baseline`: the N = 1e4 d = 1
+    workload as a mean over runs (brute force and ITM agree on K), and the
+    N = 1e6 d = 1 / d = 2 workloads on all cores and on one, each with a
+    whole-match time extrapolated from a bounded sample."""
+    import bench
+    sc = bench.cpu_small_configs(reps=2)
+    assert sc["runs"] == 2 and sc["K"] > 0 and sc["cores"] >= 1
+    assert sc["bf_1core_s"] > 0 and sc["itm_1core_s"] > 0 and sc["itm_all_cores_s"] > 0
+    rows = bench.cpu_config2(budget_s=0.2)
+    names = [r["workload"] for r in rows]
+    assert names == [f"uniform_d{d}_N1e6_a{a}" for d in (1, 2) for a in ("0.01", "1", "100")]
+    for r in rows:
+        assert r["match_s_all_cores"] > 0 and r["match_s_one_core"] > 0 and r["cores"] >= 1
+        assert r["pairs_per_s_all_cores"] >= 0 and "one thread" in r["sample"]
